@@ -1,0 +1,257 @@
+"""Benchmark: hafnian subset-terms/s at n = 48 (complex128) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--n 48] [--impl reference]
+
+One step is one complete hafnian of a seeded complex Gaussian symmetric
+48 x 48 matrix: all 2^24 subset terms of the signed sum (Sec. 3.2, eq. main),
+each by Householder-Hessenberg + La Budde + power series on the GPU.
+
+Printed (rank 0, one JSON line):
+  value   subset-terms/s over all ranks, device-resident input, CUDA-event
+          timed on the launching stream (L2 flushed between steps);
+  e2e     the same metric through the host-pointer C entry point haf_c128,
+          pinned host input copied in and the result read back every step;
+  roofline  FP64 pipe: algorithmic flops of the step (44/3) 2^h h^2 (h+3)
+          over the measured step time, against the FP64 DFMA rate measured
+          live on the same GPU by the library's probe kernel;
+  cpu_baseline  the binary128 CPU oracle on a bounded sample of the same
+          workload's subsets, on the host's cores.
+Multi-GPU (torchrun): each rank computes its own hafnian (independent
+problems, no collective on the data path): weak scaling.
+``--impl reference``: the oracle itself, timed on the host cores (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "subset-terms/s (haf, n=48, complex128)"
+UNIT = "subset-terms/s"
+
+
+def alg_flops(n: int) -> float:
+    """Algorithmic FP64 flops of one hafnian: sum over subsets of the
+    Householder-Hessenberg (40/3 N^3) + La Budde (4/3 N^3) counts, N = 2|Z|:
+    (44/3) sum_m C(h,m) (2m)^3 = (44/3) 2^h h^2 (h+3)."""
+    h = n // 2
+    return (44.0 / 3.0) * (2 ** h) * h * h * (h + 3)
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(s[0]) for s in self.samples if s and s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if len(s) > 1 and s[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for k, name in enumerate(names):
+                if len(s) > 4 + k and s[4 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def cpu_baseline(n: int, seed: int, budget_s: float = 12.0):
+    """The oracle (binary128, as it stands) on a bounded random sample of
+    the workload's subsets; subset-terms/s on the host cores."""
+    import oracle
+    from paper_1805_12498_gb300 import inputs
+
+    A = inputs.complex_gaussian_symmetric(n, seed)
+    h = n // 2
+    cores = oracle.default_threads()
+    masks = inputs.random_masks(h, cores, seed + 7)
+    t = time.perf_counter()
+    oracle.terms(A, False, masks, nthreads=cores)
+    dt = time.perf_counter() - t
+    count = max(cores, int(cores * max(1.0, (budget_s - dt) / max(dt, 1e-3))))
+    masks = inputs.random_masks(h, count, seed + 8)
+    t = time.perf_counter()
+    oracle.terms(A, False, masks, nthreads=cores)
+    dt = time.perf_counter() - t
+    return {"value": count / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{count} uniformly random subsets of the n={n} seeded complex Gaussian "
+                      f"matrix, binary128 trace-power summands, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    base = cpu_baseline(args.n, args.seed, budget_s=max(5.0, 20.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    for _ in range(args.steps):
+        b = cpu_baseline(args.n, args.seed, budget_s=max(5.0, 60.0 / max(1, args.steps)))
+        vals.append(b["value"])
+    value = statistics.mean(vals) if vals else base["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f128 (binary128, CPU oracle)", "data": "synthetic",
+            "config": {"workload": f"haf of one seeded complex Gaussian symmetric {args.n}x{args.n} matrix "
+                                   f"(2^{args.n // 2} subset terms); bounded subset sample on the host"},
+            "cpu_baseline": {**base, "value": value},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--n", type=int, default=48)
+    ap.add_argument("--seed", type=int, default=48)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1805_12498_gb300 as hg
+    from paper_1805_12498_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    n, h = args.n, args.n // 2
+    A = inputs.complex_gaussian_symmetric(n, args.seed + rank)
+    dA = torch.from_numpy(A.view(np.float64).copy()).to(dev)
+    ws = hg.workspace_bytes(n)
+    work = torch.empty(ws // 8 + 64, dtype=torch.float64, device=dev)
+    wptr = (work.data_ptr() + 255) // 256 * 256
+    out = torch.zeros(5, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        hg.haf_launch(dA.data_ptr(), n, out.data_ptr(), wptr, ws, stream.cuda_stream)
+
+    peak_tflops, _ = hg.fp64_peak()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # device-resident timed region: one event pair per step on the launching stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clocks:
+        barrier()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = statistics.mean(ms)
+    res = out.cpu().numpy()
+
+    # end to end through the host-pointer entry point (pinned input, result read back)
+    pinned = torch.from_numpy(A.view(np.float64).copy()).pin_memory()
+    import ctypes
+    from paper_1805_12498_gb300 import _native
+    L = _native.lib()
+    host_out = np.zeros(2)
+    info = _native.HafInfo()
+    L.haf_c128(ctypes.cast(pinned.data_ptr(), _native._DP), n, host_out.ctypes.data_as(_native._DP),
+               ctypes.byref(info))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _native.check(L.haf_c128(ctypes.cast(pinned.data_ptr(), _native._DP), n,
+                                 host_out.ctypes.data_as(_native._DP), ctypes.byref(info)))
+    t_e2e = (time.perf_counter() - t0) / args.steps
+    barrier()
+
+    # max over ranks
+    t_dev = torch.tensor([ms_step, t_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
+    ms_step, t_e2e = float(t_dev[0]), float(t_dev[1])
+    subsets = 2 ** h
+    value = world * subsets / (ms_step * 1e-3)
+    e2e = world * subsets / t_e2e
+    achieved = alg_flops(n) / (ms_step * 1e-3) / 1e12
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (complex128, double-double subset sum)", "data": "synthetic",
+            "config": {"workload": f"haf of one seeded complex Gaussian symmetric {n}x{n} matrix per GPU "
+                                   f"(A=(G+G^T)/2, re,im ~ N(0,1/2)); 2^{h} subset terms per step",
+                       "n": n, "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"independent problems x{world}"},
+            "result": {"re": float(res[0] + res[2]), "im": float(res[1] + res[3]), "abs_sum": float(res[4])},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tflops, "traffic": None,
+                         "note": "FP64 pipe; peak = DFMA probe measured in this run (of measured)"},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": n * n * 16,
+                    "d2h_bytes_per_step": 5 * 8},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks.summary(),
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(n, args.seed)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

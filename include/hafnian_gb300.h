@@ -1,0 +1,143 @@
+/*
+ * hafnian_gb300.h -- C ABI of the GB300 (sm_103a) hafnian / loop-hafnian
+ * library.
+ *
+ * What is computed.  For an n x n complex (or real) symmetric matrix A:
+ *   haf(A)  = sum over perfect matchings M of prod_{(i,j) in M} A_ij
+ *             (Sec. 2, eq. hafA);
+ *   lhaf(A) = the same sum over single-pair matchings, in which a vertex may
+ *             also be matched to itself with weight A_ii (Sec. 2, lhaf
+ *             definition).
+ * Both are evaluated with the signed subset sum of Sec. 3.2 (eq. main):
+ *   haf(A) = sum_{Z subset of the n/2 pairs} (-1)^{n/2-|Z|} f(Z),
+ * where f(Z) is the lambda^{n/2} coefficient of the trace generating
+ * function of Sec. 3.3 (eq. poly, eq. haffinal; for lhaf the q(lambda,B,v)
+ * function).  The library obtains f(Z) = [lambda^{n/2}] det(I - lambda B)^{-1/2}
+ * (times the exponential of the loop series for lhaf) from a Householder
+ * Hessenberg reduction of B = (X A)^{(Z)}, the La Budde recurrence for the
+ * characteristic polynomial and a truncated power-series recurrence; this
+ * equals the paper's Schur/power-trace route in exact arithmetic (App. B).
+ *
+ * Input conventions (all entry points).
+ *   - A is row-major n x n.  Complex matrices are interleaved (re, im)
+ *     doubles, i.e. C99 double _Complex / numpy complex128 layout.
+ *   - Off-diagonal entries are read from the upper triangle only (i < j);
+ *     the lower triangle is never read (App. C: haf(A) = haf(A + L) for
+ *     lower-triangular L).  haf ignores the diagonal; lhaf reads it.
+ *   - n = 0 gives 1.  Odd n: haf = 0; lhaf pads A with one isolated vertex
+ *     of loop weight 1 (which leaves the single-pair-matching sum unchanged).
+ *   - Supported sizes: 0 <= n <= HAF_MAX_N.
+ *   - Pointers are owned by the caller.  Host-pointer entry points copy A to
+ *     the device themselves and return when the result is on the host.
+ *
+ * Results.  The signed subset sum is accumulated in double-double
+ * (compensated) arithmetic and reduced in a fixed order, so a result is
+ * bit-reproducible from run to run.  Alongside the value the library
+ * reports abs_sum = sum_Z |f(Z)|; the absolute error is bounded in practice
+ * by a small multiple of 1e-16 * abs_sum (the accuracy contract used by the
+ * tests is |error| <= 1e-10 * abs_sum).
+ *
+ * Errors.  Every entry point returns HAF_OK (0) or a negative HAF_E* code
+ * and never throws across the ABI.  On error the outputs are left untouched.
+ * haf_last_error() returns a short text for the calling thread's last error.
+ */
+#ifndef HAFNIAN_GB300_H
+#define HAFNIAN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HAF_MAX_N 56
+
+/* status codes */
+#define HAF_OK 0
+#define HAF_EINVAL (-1)    /* bad argument (null pointer, n out of range, bad flags) */
+#define HAF_ENOMEM (-2)    /* device or host allocation failed                     */
+#define HAF_ECUDA (-3)     /* a CUDA runtime call failed                           */
+#define HAF_ESMALL (-7)    /* caller-supplied workspace too small                  */
+
+/* flags */
+#define HAF_FLAG_LOOPS (1u << 0) /* loop hafnian (used by the *_launch forms)   */
+#define HAF_FLAG_REAL (1u << 1)  /* A is real float64, not complex128           */
+
+/* Per-call report. */
+typedef struct haf_info {
+  double abs_sum;     /* sum over subsets Z of |f(Z)|                          */
+  double value_lo[2]; /* low parts of the double-double result (re, im)        */
+  int64_t subsets;    /* number of subset terms evaluated (2^{n/2} - 1)        */
+  double seconds;     /* wall time of the call (host clock)                    */
+  int64_t launches;   /* CUDA kernels launched by the call                     */
+} haf_info;
+
+/* ------------------------------------------------------------------------
+ * Single matrix, host pointers, synchronous.
+ *   A   : n*n complex128 (haf_c128, lhaf_c128) or float64 (haf_f64, lhaf_f64)
+ *   out : 2 doubles (re, im) for the complex forms, 1 double for the real.
+ *   info: may be NULL.
+ * Passage: Sec. 3.2 eq. main with the summand of Sec. 3.3 (eq. haffinal and
+ * its loop-hafnian analogue).
+ * ---------------------------------------------------------------------- */
+int haf_c128(const double* A, int64_t n, double* out, haf_info* info);
+int lhaf_c128(const double* A, int64_t n, double* out, haf_info* info);
+int haf_f64(const double* A, int64_t n, double* out, haf_info* info);
+int lhaf_f64(const double* A, int64_t n, double* out, haf_info* info);
+
+/* ------------------------------------------------------------------------
+ * Batched: `count` independent matrices of possibly different sizes run in
+ * one persistent launch (host pointers, synchronous).
+ *   As[i]  : matrix i (n = ns[i]); complex128.
+ *   outs   : 2*count doubles; infos: count entries or NULL.
+ * Passage: eq. main applied to each matrix.
+ * ---------------------------------------------------------------------- */
+int haf_c128_batched(const double* const* As, const int64_t* ns, int64_t count, double* outs,
+                     haf_info* infos);
+int lhaf_c128_batched(const double* const* As, const int64_t* ns, int64_t count, double* outs,
+                      haf_info* infos);
+
+/* ------------------------------------------------------------------------
+ * Device-resident asynchronous form (for callers that own device memory and
+ * streams, e.g. through PyTorch).
+ *   dA        : device pointer, n*n complex128 (or float64 with HAF_FLAG_REAL)
+ *   d_out     : device pointer to 5 doubles written as
+ *               {re_hi, im_hi, re_lo, im_lo, abs_sum}
+ *   d_work    : device workspace of at least haf_workspace_bytes(n, flags)
+ *               bytes, 256-byte aligned, not shared with a concurrent call
+ *   stream    : cudaStream_t (NULL = legacy default stream)
+ * The call only enqueues work; it returns before the result is ready.
+ * Returns HAF_ESMALL if ws_bytes is too small.  n must be even, 2..HAF_MAX_N
+ * (the host entry points handle 0 and odd n).
+ * ---------------------------------------------------------------------- */
+size_t haf_workspace_bytes(int64_t n, uint32_t flags);
+int haf_launch(const double* dA, int64_t n, uint32_t flags, double* d_out, void* d_work,
+               size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Per-subset summands (for sampling checks at large n).
+ *   masks[i] : subset Z as a bitmask over the n/2 pairs (bit p <=> pair
+ *              (2p, 2p+1) in Z); host array of `count` entries.
+ *   terms    : 2*count doubles (host), receives f(Z) WITHOUT the sign
+ *              (-1)^{n/2-|Z|}.
+ *   loops    : 0 for the haf summand, 1 for the lhaf summand.
+ * Passage: the summand of eq. haffinal (Sec. 3.3).
+ * ---------------------------------------------------------------------- */
+int haf_terms_c128(const double* A, int64_t n, int loops, const uint64_t* masks, int64_t count,
+                   double* terms);
+
+/* ------------------------------------------------------------------------
+ * Utilities.
+ * ---------------------------------------------------------------------- */
+/* Measured FP64 FMA throughput of the current device, in TFLOP/s (2 flops
+ * per FMA), from a dependent-chain DFMA kernel over all SMs; ms is the
+ * kernel time.  Used as the roofline denominator. */
+int haf_fp64_peak(double* tflops, double* ms);
+const char* haf_last_error(void);
+const char* haf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HAFNIAN_GB300_H */

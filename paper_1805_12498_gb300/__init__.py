@@ -1,0 +1,129 @@
+"""GB300-native (sm_103a) hafnian and loop hafnian.
+
+Python front end of the C ABI in include/hafnian_gb300.h.  Every number is
+computed by the CUDA library; this module only marshals arguments.
+
+    >>> import numpy as np, paper_1805_12498_gb300 as hg
+    >>> hg.haf(np.ones((16, 16)))            # (16-1)!! = 2027025
+    >>> hg.lhaf(np.ones((16, 16)))           # T(16) = 46206736
+
+The hafnian is the sum over perfect matchings of the products of the
+matched entries (Sec. 2); it is evaluated with the O(n^3 2^{n/2}) signed
+subset sum of Sec. 3 on the GPU in FP64 with double-double accumulation.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _native
+from ._native import HAF_FLAG_LOOPS, HAF_FLAG_REAL, HAF_MAX_N, HafError  # noqa: F401
+
+__all__ = ["haf", "lhaf", "haf_info", "haf_batched", "haf_terms", "workspace_bytes",
+           "haf_launch", "fp64_peak", "HafError", "HAF_MAX_N"]
+
+
+@dataclass
+class Info:
+    value: complex
+    abs_sum: float
+    value_lo: complex
+    subsets: int
+    seconds: float
+    launches: int
+
+
+def _prep(A, real: bool) -> np.ndarray:
+    A = np.asarray(A)
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be a square matrix")
+    return np.ascontiguousarray(A, dtype=np.float64 if real else np.complex128)
+
+
+def haf_info(A, loops: bool = False, real: bool | None = None) -> Info:
+    """Hafnian (or loop hafnian) of A with the per-call report."""
+    if real is None:
+        real = not np.iscomplexobj(A)
+    A = _prep(A, real)
+    L = _native.lib()
+    fn = {(False, False): L.haf_c128, (True, False): L.lhaf_c128,
+          (False, True): L.haf_f64, (True, True): L.lhaf_f64}[(bool(loops), bool(real))]
+    out = np.zeros(2)
+    info = _native.HafInfo()
+    _native.check(fn(A.ctypes.data_as(_native._DP), A.shape[0], out.ctypes.data_as(_native._DP),
+                     ctypes.byref(info)))
+    val = complex(out[0], 0.0 if real else out[1])
+    return Info(val, info.abs_sum, complex(info.value_lo[0], info.value_lo[1]), info.subsets,
+                info.seconds, info.launches)
+
+
+def haf(A, loops: bool = False):
+    """haf(A) (Sec. 2, eq. hafA).  Real input gives a float, complex a complex."""
+    r = haf_info(A, loops)
+    return r.value.real if not np.iscomplexobj(A) else r.value
+
+
+def lhaf(A):
+    """Loop hafnian lhaf(A) (Sec. 2)."""
+    return haf(A, loops=True)
+
+
+def haf_batched(mats, loops: bool = False, with_info: bool = False):
+    """Hafnians of a list of complex matrices of mixed sizes in one launch."""
+    mats = [_prep(M, False) for M in mats]
+    count = len(mats)
+    ptrs = (_native._DP * max(1, count))(*[M.ctypes.data_as(_native._DP) for M in mats])
+    ns = np.array([M.shape[0] for M in mats], dtype=np.int64)
+    outs = np.zeros(2 * max(1, count))
+    infos = (_native.HafInfo * max(1, count))()
+    L = _native.lib()
+    fn = L.lhaf_c128_batched if loops else L.haf_c128_batched
+    _native.check(fn(ptrs, ns.ctypes.data_as(_native._I64P), count, outs.ctypes.data_as(_native._DP), infos))
+    vals = outs[0:2 * count:2] + 1j * outs[1:2 * count:2]
+    if not with_info:
+        return vals
+    return vals, [Info(complex(vals[i]), infos[i].abs_sum, complex(*infos[i].value_lo), infos[i].subsets,
+                       infos[i].seconds, infos[i].launches) for i in range(count)]
+
+
+def haf_terms(A, masks, loops: bool = False) -> np.ndarray:
+    """Unsigned summands f(Z) for the given subset bitmasks (Sec. 3.3)."""
+    A = _prep(A, False)
+    masks = np.ascontiguousarray(np.asarray(masks, dtype=np.uint64))
+    out = np.zeros(2 * max(1, masks.size))
+    _native.check(_native.lib().haf_terms_c128(
+        A.ctypes.data_as(_native._DP), A.shape[0], int(bool(loops)),
+        masks.ctypes.data_as(_native._U64P), masks.size, out.ctypes.data_as(_native._DP)))
+    return out[0:2 * masks.size:2] + 1j * out[1:2 * masks.size:2]
+
+
+def workspace_bytes(n: int, loops: bool = False, real: bool = False) -> int:
+    flags = (HAF_FLAG_LOOPS if loops else 0) | (HAF_FLAG_REAL if real else 0)
+    b = _native.lib().haf_workspace_bytes(n, flags)
+    if b == 0:
+        raise HafError(_native.HAF_EINVAL, f"no workspace size for n={n}")
+    return int(b)
+
+
+def haf_launch(dA_ptr: int, n: int, d_out_ptr: int, d_work_ptr: int, ws_bytes: int,
+               stream_ptr: int = 0, loops: bool = False, real: bool = False) -> None:
+    """Enqueue a hafnian on device memory (raw pointers, e.g. torch
+    ``tensor.data_ptr()`` and ``torch.cuda.current_stream().cuda_stream``).
+    The 5-double record {re_hi, im_hi, re_lo, im_lo, abs_sum} lands at
+    d_out_ptr when the stream reaches it."""
+    flags = (HAF_FLAG_LOOPS if loops else 0) | (HAF_FLAG_REAL if real else 0)
+    _native.check(_native.lib().haf_launch(dA_ptr, n, flags, d_out_ptr, d_work_ptr, ws_bytes, stream_ptr))
+
+
+def fp64_peak() -> tuple[float, float]:
+    """(TFLOP/s, ms) of the library's DFMA throughput probe on this GPU."""
+    t = ctypes.c_double()
+    ms = ctypes.c_double()
+    _native.check(_native.lib().haf_fp64_peak(ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
+
+
+def version() -> str:
+    return _native.lib().haf_version().decode()

@@ -1,0 +1,90 @@
+"""ctypes binding of the C ABI in include/hafnian_gb300.h (argument
+marshalling only: every step of the hafnian runs in the CUDA library).
+
+The shared library is built in-tree by ``paper_1805_12498_gb300.build``;
+if it is missing and cannot be built, every call raises instead of falling
+back to any CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+HAF_OK = 0
+HAF_EINVAL = -1
+HAF_ENOMEM = -2
+HAF_ECUDA = -3
+HAF_ESMALL = -7
+HAF_FLAG_LOOPS = 1
+HAF_FLAG_REAL = 2
+HAF_MAX_N = 56
+
+
+class HafInfo(ctypes.Structure):
+    _fields_ = [("abs_sum", ctypes.c_double), ("value_lo", ctypes.c_double * 2),
+                ("subsets", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
+
+
+class HafError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hafnian_gb300 error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+_DP = ctypes.POINTER(ctypes.c_double)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load (building first if needed) the CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; run paper_1805_12498_gb300.build")
+        L = ctypes.CDLL(path)
+        for name in ("haf_c128", "lhaf_c128", "haf_f64", "lhaf_f64"):
+            f = getattr(L, name)
+            f.argtypes = [_DP, ctypes.c_int64, _DP, ctypes.POINTER(HafInfo)]
+            f.restype = ctypes.c_int
+        for name in ("haf_c128_batched", "lhaf_c128_batched"):
+            f = getattr(L, name)
+            f.argtypes = [ctypes.POINTER(_DP), _I64P, ctypes.c_int64, _DP, ctypes.POINTER(HafInfo)]
+            f.restype = ctypes.c_int
+        L.haf_workspace_bytes.argtypes = [ctypes.c_int64, ctypes.c_uint32]
+        L.haf_workspace_bytes.restype = ctypes.c_size_t
+        L.haf_launch.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+        L.haf_launch.restype = ctypes.c_int
+        L.haf_terms_c128.argtypes = [_DP, ctypes.c_int64, ctypes.c_int, _U64P, ctypes.c_int64, _DP]
+        L.haf_terms_c128.restype = ctypes.c_int
+        L.haf_fp64_peak.argtypes = [_DP, _DP]
+        L.haf_fp64_peak.restype = ctypes.c_int
+        L.haf_last_error.argtypes = []
+        L.haf_last_error.restype = ctypes.c_char_p
+        L.haf_version.argtypes = []
+        L.haf_version.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def check(rc: int) -> None:
+    if rc != HAF_OK:
+        msg = lib().haf_last_error()
+        raise HafError(rc, msg.decode() if msg else "")

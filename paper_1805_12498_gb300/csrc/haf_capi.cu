@@ -1,0 +1,684 @@
+// haf_capi.cu -- host side of the C ABI declared in include/hafnian_gb300.h:
+// argument checks, the work plan (subset chunks per size |Z|), device
+// buffers, launches and the read-back of results.
+//
+// Plan.  For a matrix of size n (h = n/2 pairs), subsets of size m = 1..h
+// (the empty subset contributes 0 for h >= 1) are grouped into chunks of
+// consecutive colex ranks.  Each size gets a lane-group width G (1..32
+// lanes per subset, 32/G subsets per warp), the smallest that fits the
+// warp's shared-memory slice, and chunks are ordered largest-work-first so
+// the persistent warps finish together.  Each chunk writes one partial;
+// partials are reduced in chunk order, independent of scheduling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/hafnian_gb300.h"
+#include "haf_internal.h"
+
+using namespace hafgb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define HAF_CUDA(call)                                                                    \
+  do {                                                                                    \
+    cudaError_t _e = (call);                                                              \
+    if (_e != cudaSuccess)                                                                \
+      return fail(HAF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e));         \
+  } while (0)
+
+uint64_t binom(int a, int b) {
+  if (b < 0 || b > a) return 0;
+  uint64_t r = 1;
+  for (int i = 1; i <= b; ++i) r = r * (uint64_t)(a - b + i) / (uint64_t)i;
+  return r;
+}
+
+// Colex unranking: the rank-th m-subset of {0..h-1} (combinatorial number system).
+uint64_t unrank_colex(uint64_t rank, int m, int h) {
+  uint64_t mask = 0;
+  int c = h - 1;
+  for (int i = m; i >= 1; --i) {
+    while (binom(c, i) > rank) --c;
+    mask |= 1ull << c;
+    rank -= binom(c, i);
+    --c;
+  }
+  return mask;
+}
+
+struct SizeCfg {
+  int G;
+  int ld;
+};
+
+// Smallest lane-group width whose S = 32/G subsets fit the warp slice.
+bool choose_cfg(int N, int h, int elem, SizeCfg* out) {
+  for (int ld : {N + 1, N}) {
+    for (int G = 1; G <= 32; G *= 2) {
+      const int S = 32 / G;
+      if ((long)S * subset_bytes(N, ld, h, elem) <= kWarpBytes) {
+        out->G = G;
+        out->ld = ld;
+        return true;
+      }
+    }
+  }
+  return false;
+}
+
+struct JobSpec {
+  int n;
+  int loops;
+  int is_real;
+};
+
+struct Plan {
+  std::vector<Chunk> chunks;
+  std::vector<int> order;
+  std::vector<int> job_begin;  // njobs + 1
+  int64_t subsets = 0;
+};
+
+int build_plan(const std::vector<JobSpec>& jobs, int num_warps, Plan* plan) {
+  plan->chunks.clear();
+  plan->order.clear();
+  plan->job_begin.assign(1, 0);
+  // total work (in N^3 units) to size the chunks
+  double total = 0.0;
+  for (const JobSpec& js : jobs) {
+    const int h = js.n / 2;
+    for (int m = 1; m <= h; ++m) total += (double)binom(h, m) * std::pow(2.0 * m, 3);
+  }
+  const double target = std::max(1.0, total / (double)(num_warps * 8));
+  std::vector<double> cost;
+  for (size_t jb = 0; jb < jobs.size(); ++jb) {
+    const JobSpec& js = jobs[jb];
+    const int h = js.n / 2;
+    const int elem = js.is_real ? 8 : 16;
+    for (int m = 1; m <= h; ++m) {
+      const int N = 2 * m;
+      SizeCfg cfg;
+      if (!choose_cfg(N, h, elem, &cfg)) return fail(HAF_EINVAL, "matrix too large for the shared-memory plan");
+      const int S = 32 / cfg.G;
+      const uint64_t cnt = binom(h, m);
+      const double per = std::pow((double)N, 3);
+      uint64_t csz = (uint64_t)std::ceil(target / per / S) * S;
+      csz = std::max<uint64_t>(csz, (uint64_t)S);
+      csz = std::min<uint64_t>(csz, (uint64_t)1 << 30);
+      for (uint64_t r0 = 0; r0 < cnt; r0 += csz) {
+        Chunk c;
+        std::memset(&c, 0, sizeof(c));
+        c.rank0 = r0;
+        c.mask0 = unrank_colex(r0, m, h);
+        c.count = (uint32_t)std::min<uint64_t>(csz, cnt - r0);
+        c.job = (uint16_t)jb;
+        c.m = (uint8_t)m;
+        c.G = (uint8_t)cfg.G;
+        c.ld = (uint8_t)cfg.ld;
+        plan->chunks.push_back(c);
+        cost.push_back((double)c.count * per * (js.loops ? 1.3 : 1.0) / (js.is_real ? 4.0 : 1.0));
+      }
+      plan->subsets += (int64_t)cnt;
+    }
+    plan->job_begin.push_back((int)plan->chunks.size());
+  }
+  plan->order.resize(plan->chunks.size());
+  for (size_t i = 0; i < plan->order.size(); ++i) plan->order[i] = (int)i;
+  std::stable_sort(plan->order.begin(), plan->order.end(),
+                   [&](int a, int b) { return cost[a] > cost[b]; });
+  return HAF_OK;
+}
+
+// Device-resident copy of a plan.
+struct DevPlan {
+  Chunk* chunks = nullptr;
+  int* order = nullptr;
+  int* job_begin = nullptr;
+  int nchunks = 0;
+  int njobs = 0;
+  int64_t subsets = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Device {
+  int id = -1;
+  int sms = 0;
+  bool configured = false;
+  cudaStream_t stream = nullptr;
+  double* tables = nullptr;
+  // growable scratch for the host-pointer entry points
+  void* work = nullptr;
+  size_t work_bytes = 0;
+  double* host_out = nullptr;  // pinned, grows
+  size_t host_out_n = 0;
+  std::map<std::tuple<int, int, int>, DevPlan> plans;  // (n, loops, real) -> plan
+};
+
+std::mutex g_mu;
+std::map<int, std::unique_ptr<Device>> g_devices;
+
+int get_device(Device** out) {
+  int id = 0;
+  HAF_CUDA(cudaGetDevice(&id));
+  auto it = g_devices.find(id);
+  if (it != g_devices.end()) {
+    *out = it->second.get();
+    return HAF_OK;
+  }
+  std::unique_ptr<Device> d(new Device());
+  d->id = id;
+  HAF_CUDA(cudaDeviceGetAttribute(&d->sms, cudaDevAttrMultiProcessorCount, id));
+  HAF_CUDA(configure_kernels());
+  HAF_CUDA(cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking));
+  std::vector<double> tab(256, 0.0);
+  for (int k = 0; k < 128; ++k) tab[k] = 0.5 * k;
+  for (int k = 1; k < 128; ++k) tab[128 + k] = 1.0 / k;
+  HAF_CUDA(cudaMalloc(&d->tables, 256 * sizeof(double)));
+  HAF_CUDA(cudaMemcpy(d->tables, tab.data(), 256 * sizeof(double), cudaMemcpyHostToDevice));
+  *out = d.get();
+  g_devices[id] = std::move(d);
+  return HAF_OK;
+}
+
+int upload_plan(const Plan& p, cudaStream_t st, DevPlan* dp) {
+  dp->nchunks = (int)p.chunks.size();
+  dp->njobs = (int)p.job_begin.size() - 1;
+  dp->subsets = p.subsets;
+  HAF_CUDA(cudaMalloc(&dp->chunks, std::max<size_t>(1, p.chunks.size()) * sizeof(Chunk)));
+  HAF_CUDA(cudaMalloc(&dp->order, std::max<size_t>(1, p.order.size()) * sizeof(int)));
+  HAF_CUDA(cudaMalloc(&dp->job_begin, p.job_begin.size() * sizeof(int)));
+  HAF_CUDA(cudaMemcpyAsync(dp->chunks, p.chunks.data(), p.chunks.size() * sizeof(Chunk),
+                           cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemcpyAsync(dp->order, p.order.data(), p.order.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemcpyAsync(dp->job_begin, p.job_begin.data(), p.job_begin.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaStreamSynchronize(st));
+  return HAF_OK;
+}
+
+void free_plan(DevPlan* dp) {
+  cudaFree(dp->chunks);
+  cudaFree(dp->order);
+  cudaFree(dp->job_begin);
+  *dp = DevPlan();
+}
+
+int cached_plan(Device* d, int n, int loops, int is_real, DevPlan** out) {
+  auto key = std::make_tuple(n, loops, is_real);
+  auto it = d->plans.find(key);
+  if (it != d->plans.end()) {
+    *out = &it->second;
+    return HAF_OK;
+  }
+  Plan p;
+  int rc = build_plan({JobSpec{n, loops, is_real}}, d->sms * kWarpsPerBlock, &p);
+  if (rc) return rc;
+  DevPlan dp;
+  rc = upload_plan(p, d->stream, &dp);
+  if (rc) return rc;
+  d->plans[key] = dp;
+  *out = &d->plans[key];
+  return HAF_OK;
+}
+
+// Workspace layout for one single-matrix launch.
+struct WsLayout {
+  size_t at, diag, partials, counter, total;
+};
+WsLayout ws_layout(int n, int nchunks) {
+  WsLayout w;
+  size_t off = 0;
+  w.at = off;
+  off += align256((size_t)n * n * 16);
+  w.diag = off;
+  off += align256((size_t)n * 16);
+  w.partials = off;
+  off += align256((size_t)std::max(1, nchunks) * 5 * sizeof(double));
+  w.counter = off;
+  off += 256;
+  w.total = off;
+  return w;
+}
+
+int ensure_work(Device* d, size_t bytes) {
+  if (d->work_bytes >= bytes) return HAF_OK;
+  if (d->work) cudaFree(d->work);
+  d->work = nullptr;
+  d->work_bytes = 0;
+  cudaError_t e = cudaMalloc(&d->work, bytes);
+  if (e != cudaSuccess) return fail(HAF_ENOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+  d->work_bytes = bytes;
+  return HAF_OK;
+}
+
+int ensure_host_out(Device* d, size_t ndoubles) {
+  if (d->host_out_n >= ndoubles) return HAF_OK;
+  if (d->host_out) cudaFreeHost(d->host_out);
+  d->host_out = nullptr;
+  d->host_out_n = 0;
+  HAF_CUDA(cudaMallocHost(&d->host_out, ndoubles * sizeof(double)));
+  d->host_out_n = ndoubles;
+  return HAF_OK;
+}
+
+// Enqueue prep + subset kernel + finalize for a plan whose jobs' At/diag
+// already sit in device memory.
+int enqueue(Device* d, const DevPlan& dp, const std::vector<Job>& jobs_host, Job* jobs_dev,
+            double* partials, int* counter, double* d_out, int is_real, cudaStream_t st,
+            const uint64_t* masks = nullptr, double* terms_out = nullptr) {
+  HAF_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host.data(), jobs_host.size() * sizeof(Job),
+                           cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+  KernelArgs a;
+  a.jobs = jobs_dev;
+  a.chunks = dp.chunks;
+  a.order = dp.order;
+  a.nchunks = dp.nchunks;
+  a.counter = counter;
+  a.partials = partials;
+  a.tables = d->tables;
+  a.masks = masks;
+  a.terms_out = terms_out;
+  a.warp_bytes = kWarpBytes;
+  const int grid = std::max(1, std::min(d->sms, (dp.nchunks + kWarpsPerBlock - 1) / kWarpsPerBlock));
+  HAF_CUDA(launch_subsets(a, is_real, grid, st));
+  if (!terms_out) HAF_CUDA(launch_finalize(partials, dp.job_begin, dp.njobs, d_out, st));
+  return HAF_OK;
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Synchronous single matrix from host memory.
+int run_single(const double* A, int64_t n64, int loops, int is_real, double* out, haf_info* info) {
+  const double t0 = now_s();
+  if (n64 < 0 || n64 > kMaxN) return fail(HAF_EINVAL, "n out of range");
+  if (!out || (n64 > 0 && !A)) return fail(HAF_EINVAL, "null pointer");
+  int n = (int)n64;
+  const int elem = is_real ? 1 : 2;
+  auto write = [&](double re, double im, double lre, double lim, double abs_sum, int64_t subsets,
+                   int64_t launches) {
+    out[0] = re;
+    if (!is_real) out[1] = im;
+    if (info) {
+      info->abs_sum = abs_sum;
+      info->value_lo[0] = lre;
+      info->value_lo[1] = lim;
+      info->subsets = subsets;
+      info->seconds = now_s() - t0;
+      info->launches = launches;
+    }
+  };
+  if (n == 0) {
+    write(1.0, 0.0, 0.0, 0.0, 1.0, 0, 0);
+    return HAF_OK;
+  }
+  std::vector<double> padded;
+  if (n & 1) {
+    if (!loops) {
+      write(0.0, 0.0, 0.0, 0.0, 0.0, 0, 0);
+      return HAF_OK;
+    }
+    // lhaf: append an isolated vertex with loop weight 1.
+    const int np = n + 1;
+    padded.assign((size_t)np * np * elem, 0.0);
+    for (int i = 0; i < n; ++i)
+      std::memcpy(&padded[(size_t)i * np * elem], A + (size_t)i * n * elem, (size_t)n * elem * sizeof(double));
+    padded[((size_t)n * np + n) * elem] = 1.0;
+    A = padded.data();
+    n = np;
+    if (n > kMaxN) return fail(HAF_EINVAL, "n out of range");
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device* d;
+  int rc = get_device(&d);
+  if (rc) return rc;
+  DevPlan* dp;
+  rc = cached_plan(d, n, loops, is_real, &dp);
+  if (rc) return rc;
+  WsLayout w = ws_layout(n, dp->nchunks);
+  const size_t jobs_off = w.total;
+  const size_t out_off = jobs_off + 256;
+  const size_t stage_off = out_off + 256;
+  const size_t abytes = (size_t)n * n * elem * sizeof(double);
+  rc = ensure_work(d, stage_off + align256(abytes));
+  if (rc) return rc;
+  rc = ensure_host_out(d, 5);
+  if (rc) return rc;
+  char* base = (char*)d->work;
+  double* At = (double*)(base + w.at);
+  double* diag = (double*)(base + w.diag);
+  double* Ad = (double*)(base + stage_off);
+  cudaStream_t st = d->stream;
+  HAF_CUDA(cudaMemcpyAsync(Ad, A, abytes, cudaMemcpyHostToDevice, st));
+  HAF_CUDA(launch_prep(Ad, n, is_real, At, diag, st));
+  std::vector<Job> jobs{Job{At, diag, n, loops}};
+  rc = enqueue(d, *dp, jobs, (Job*)(base + jobs_off), (double*)(base + w.partials),
+               (int*)(base + w.counter), (double*)(base + out_off), is_real, st);
+  if (rc) return rc;
+  HAF_CUDA(cudaMemcpyAsync(d->host_out, base + out_off, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  HAF_CUDA(cudaStreamSynchronize(st));
+  const double* o = d->host_out;
+  write(o[0] + o[2], o[1] + o[3], o[2], o[3], o[4], dp->subsets, 3);
+  return HAF_OK;
+}
+
+int run_batched(const double* const* As, const int64_t* ns, int64_t count, int loops, double* outs,
+                haf_info* infos) {
+  const double t0 = now_s();
+  if (count < 0 || (count > 0 && (!As || !ns || !outs))) return fail(HAF_EINVAL, "null pointer");
+  if (count > 65535) return fail(HAF_EINVAL, "batch too large (max 65535 matrices per call)");
+  std::vector<JobSpec> specs;
+  std::vector<int64_t> idx;  // job -> batch index
+  std::vector<std::vector<double>> pads;
+  std::vector<const double*> srcs;
+  for (int64_t b = 0; b < count; ++b) {
+    int64_t n = ns[b];
+    if (n < 0 || n > kMaxN || (n > 0 && !As[b])) return fail(HAF_EINVAL, "bad matrix in batch");
+  }
+  for (int64_t b = 0; b < count; ++b) {
+    int n = (int)ns[b];
+    const double* A = As[b];
+    if (n == 0) {
+      outs[2 * b] = 1.0;
+      outs[2 * b + 1] = 0.0;
+      if (infos) infos[b] = haf_info{1.0, {0.0, 0.0}, 0, 0.0, 0};
+      continue;
+    }
+    if (n & 1) {
+      if (!loops) {
+        outs[2 * b] = 0.0;
+        outs[2 * b + 1] = 0.0;
+        if (infos) infos[b] = haf_info{0.0, {0.0, 0.0}, 0, 0.0, 0};
+        continue;
+      }
+      const int np = n + 1;
+      if (np > kMaxN) return fail(HAF_EINVAL, "n out of range");
+      std::vector<double> p((size_t)np * np * 2, 0.0);
+      for (int i = 0; i < n; ++i) std::memcpy(&p[(size_t)i * np * 2], A + (size_t)i * n * 2, (size_t)n * 2 * sizeof(double));
+      p[((size_t)n * np + n) * 2] = 1.0;
+      pads.push_back(std::move(p));
+      A = pads.back().data();
+      n = np;
+    }
+    specs.push_back(JobSpec{n, loops, 0});
+    idx.push_back(b);
+    srcs.push_back(A);
+  }
+  if (specs.empty()) return HAF_OK;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device* d;
+  int rc = get_device(&d);
+  if (rc) return rc;
+  Plan p;
+  rc = build_plan(specs, d->sms * kWarpsPerBlock, &p);
+  if (rc) return rc;
+  const int njobs = (int)specs.size();
+  // layout: per job A (staging), At, diag; then jobs, partials, counter, out, plan arrays
+  std::vector<size_t> a_off(njobs), at_off(njobs), dg_off(njobs);
+  size_t off = 0;
+  for (int j = 0; j < njobs; ++j) {
+    const size_t nn = (size_t)specs[j].n * specs[j].n * 16;
+    a_off[j] = off;
+    off += align256(nn);
+    at_off[j] = off;
+    off += align256(nn);
+    dg_off[j] = off;
+    off += align256((size_t)specs[j].n * 16);
+  }
+  const size_t jobs_off = off;
+  off += align256(njobs * sizeof(Job));
+  const size_t part_off = off;
+  off += align256(p.chunks.size() * 5 * sizeof(double));
+  const size_t cnt_off = off;
+  off += 256;
+  const size_t out_off = off;
+  off += align256((size_t)njobs * 5 * sizeof(double));
+  const size_t ch_off = off;
+  off += align256(p.chunks.size() * sizeof(Chunk));
+  const size_t ord_off = off;
+  off += align256(p.order.size() * sizeof(int));
+  const size_t jb_off = off;
+  off += align256(p.job_begin.size() * sizeof(int));
+  rc = ensure_work(d, off);
+  if (rc) return rc;
+  rc = ensure_host_out(d, (size_t)njobs * 5);
+  if (rc) return rc;
+  char* base = (char*)d->work;
+  cudaStream_t st = d->stream;
+  std::vector<Job> jobs(njobs);
+  for (int j = 0; j < njobs; ++j) {
+    const int n = specs[j].n;
+    HAF_CUDA(cudaMemcpyAsync(base + a_off[j], srcs[j], (size_t)n * n * 16, cudaMemcpyHostToDevice, st));
+    HAF_CUDA(launch_prep((double*)(base + a_off[j]), n, 0, (double*)(base + at_off[j]),
+                         (double*)(base + dg_off[j]), st));
+    jobs[j] = Job{(double*)(base + at_off[j]), (double*)(base + dg_off[j]), n, loops};
+  }
+  DevPlan dp;
+  dp.chunks = (Chunk*)(base + ch_off);
+  dp.order = (int*)(base + ord_off);
+  dp.job_begin = (int*)(base + jb_off);
+  dp.nchunks = (int)p.chunks.size();
+  dp.njobs = njobs;
+  dp.subsets = p.subsets;
+  HAF_CUDA(cudaMemcpyAsync(dp.chunks, p.chunks.data(), p.chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemcpyAsync(dp.order, p.order.data(), p.order.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemcpyAsync(dp.job_begin, p.job_begin.data(), p.job_begin.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  rc = enqueue(d, dp, jobs, (Job*)(base + jobs_off), (double*)(base + part_off), (int*)(base + cnt_off),
+               (double*)(base + out_off), 0, st);
+  if (rc) return rc;
+  HAF_CUDA(cudaMemcpyAsync(d->host_out, base + out_off, (size_t)njobs * 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  HAF_CUDA(cudaStreamSynchronize(st));
+  const double secs = now_s() - t0;
+  for (int j = 0; j < njobs; ++j) {
+    const double* o = d->host_out + 5 * j;
+    const int64_t b = idx[j];
+    outs[2 * b] = o[0] + o[2];
+    outs[2 * b + 1] = o[1] + o[3];
+    if (infos) {
+      const int h = specs[j].n / 2;
+      infos[b] = haf_info{o[4], {o[2], o[3]}, (int64_t)((1ull << h) - 1), secs, (int64_t)(njobs + 2)};
+    }
+  }
+  return HAF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int haf_c128(const double* A, int64_t n, double* out, haf_info* info) { return run_single(A, n, 0, 0, out, info); }
+int lhaf_c128(const double* A, int64_t n, double* out, haf_info* info) { return run_single(A, n, 1, 0, out, info); }
+int haf_f64(const double* A, int64_t n, double* out, haf_info* info) { return run_single(A, n, 0, 1, out, info); }
+int lhaf_f64(const double* A, int64_t n, double* out, haf_info* info) { return run_single(A, n, 1, 1, out, info); }
+
+int haf_c128_batched(const double* const* As, const int64_t* ns, int64_t count, double* outs, haf_info* infos) {
+  return run_batched(As, ns, count, 0, outs, infos);
+}
+int lhaf_c128_batched(const double* const* As, const int64_t* ns, int64_t count, double* outs, haf_info* infos) {
+  return run_batched(As, ns, count, 1, outs, infos);
+}
+
+size_t haf_workspace_bytes(int64_t n, uint32_t flags) {
+  if (n < 2 || n > kMaxN || (n & 1)) return 0;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device* d;
+  if (get_device(&d)) return 0;
+  DevPlan* dp;
+  if (cached_plan(d, (int)n, (flags & HAF_FLAG_LOOPS) ? 1 : 0, (flags & HAF_FLAG_REAL) ? 1 : 0, &dp)) return 0;
+  return ws_layout((int)n, dp->nchunks).total + 256;
+}
+
+int haf_launch(const double* dA, int64_t n, uint32_t flags, double* d_out, void* d_work, size_t ws_bytes,
+               void* stream) {
+  if (n < 2 || n > kMaxN || (n & 1)) return fail(HAF_EINVAL, "haf_launch: n must be even, 2..HAF_MAX_N");
+  if (!dA || !d_out || !d_work) return fail(HAF_EINVAL, "haf_launch: null pointer");
+  if (((uintptr_t)d_work & 255) != 0) return fail(HAF_EINVAL, "haf_launch: workspace not 256-byte aligned");
+  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL)) return fail(HAF_EINVAL, "haf_launch: unknown flags");
+  const int loops = (flags & HAF_FLAG_LOOPS) ? 1 : 0, is_real = (flags & HAF_FLAG_REAL) ? 1 : 0;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device* d;
+  int rc = get_device(&d);
+  if (rc) return rc;
+  DevPlan* dp;
+  rc = cached_plan(d, (int)n, loops, is_real, &dp);
+  if (rc) return rc;
+  WsLayout w = ws_layout((int)n, dp->nchunks);
+  if (ws_bytes < w.total + 256) return fail(HAF_ESMALL, "haf_launch: workspace too small");
+  char* base = (char*)d_work;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* At = (double*)(base + w.at);
+  double* diag = (double*)(base + w.diag);
+  HAF_CUDA(launch_prep(dA, (int)n, is_real, At, diag, st));
+  std::vector<Job> jobs{Job{At, diag, (int)n, loops}};
+  return enqueue(d, *dp, jobs, (Job*)(base + w.total), (double*)(base + w.partials), (int*)(base + w.counter),
+                 d_out, is_real, st);
+}
+
+int haf_terms_c128(const double* A, int64_t n64, int loops, const uint64_t* masks, int64_t count, double* terms) {
+  if (n64 < 2 || n64 > kMaxN || (n64 & 1)) return fail(HAF_EINVAL, "haf_terms_c128: n must be even, 2..HAF_MAX_N");
+  if (!A || (count > 0 && (!masks || !terms)) || count < 0) return fail(HAF_EINVAL, "haf_terms_c128: bad arguments");
+  const int n = (int)n64, h = n / 2;
+  for (int64_t i = 0; i < count; ++i)
+    if (masks[i] >> h) return fail(HAF_EINVAL, "haf_terms_c128: mask has bits beyond n/2");
+  if (count == 0) return HAF_OK;
+  // sort subsets by size; each size becomes chunks of one group-round each
+  std::vector<int64_t> perm(count);
+  for (int64_t i = 0; i < count; ++i) perm[i] = i;
+  std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) {
+    return __builtin_popcountll(masks[a]) < __builtin_popcountll(masks[b]);
+  });
+  std::vector<uint64_t> sorted(count);
+  for (int64_t i = 0; i < count; ++i) sorted[i] = masks[perm[i]];
+  Plan p;
+  p.job_begin = {0};
+  int64_t i = 0;
+  while (i < count) {
+    const int m = __builtin_popcountll(sorted[i]);
+    int64_t e = i;
+    while (e < count && __builtin_popcountll(sorted[e]) == m) ++e;
+    if (m == 0) {  // empty subset: f = 0 for h >= 1
+      i = e;
+      continue;
+    }
+    SizeCfg cfg;
+    if (!choose_cfg(2 * m, h, 16, &cfg)) return fail(HAF_EINVAL, "haf_terms_c128: size too large");
+    const int S = 32 / cfg.G;
+    for (int64_t r = i; r < e; r += 4 * S) {
+      Chunk c;
+      std::memset(&c, 0, sizeof(c));
+      c.rank0 = (uint64_t)r;
+      c.count = (uint32_t)std::min<int64_t>(4 * S, e - r);
+      c.m = (uint8_t)m;
+      c.G = (uint8_t)cfg.G;
+      c.ld = (uint8_t)cfg.ld;
+      p.chunks.push_back(c);
+    }
+    i = e;
+  }
+  p.job_begin.push_back((int)p.chunks.size());
+  p.order.resize(p.chunks.size());
+  for (size_t q = 0; q < p.order.size(); ++q) p.order[q] = (int)q;
+  std::vector<double> res((size_t)count * 2, 0.0);
+  if (!p.chunks.empty()) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    Device* d;
+    int rc = get_device(&d);
+    if (rc) return rc;
+    const size_t nn = (size_t)n * n * 16;
+    size_t off = 0;
+    const size_t a_off = off; off += align256(nn);
+    const size_t at_off = off; off += align256(nn);
+    const size_t dg_off = off; off += align256((size_t)n * 16);
+    const size_t mk_off = off; off += align256((size_t)count * 8);
+    const size_t tm_off = off; off += align256((size_t)count * 16);
+    const size_t ch_off = off; off += align256(p.chunks.size() * sizeof(Chunk));
+    const size_t ord_off = off; off += align256(p.order.size() * sizeof(int));
+    const size_t jb_off = off; off += 256;
+    const size_t job_off = off; off += 256;
+    const size_t cnt_off = off; off += 256;
+    rc = ensure_work(d, off);
+    if (rc) return rc;
+    char* base = (char*)d->work;
+    cudaStream_t st = d->stream;
+    HAF_CUDA(cudaMemcpyAsync(base + a_off, A, nn, cudaMemcpyHostToDevice, st));
+    HAF_CUDA(launch_prep((double*)(base + a_off), n, 0, (double*)(base + at_off), (double*)(base + dg_off), st));
+    HAF_CUDA(cudaMemcpyAsync(base + mk_off, sorted.data(), (size_t)count * 8, cudaMemcpyHostToDevice, st));
+    HAF_CUDA(cudaMemsetAsync(base + tm_off, 0, (size_t)count * 16, st));
+    DevPlan dp;
+    dp.chunks = (Chunk*)(base + ch_off);
+    dp.order = (int*)(base + ord_off);
+    dp.job_begin = (int*)(base + jb_off);
+    dp.nchunks = (int)p.chunks.size();
+    dp.njobs = 1;
+    HAF_CUDA(cudaMemcpyAsync(dp.chunks, p.chunks.data(), p.chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice, st));
+    HAF_CUDA(cudaMemcpyAsync(dp.order, p.order.data(), p.order.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    std::vector<Job> jobs{Job{(double*)(base + at_off), (double*)(base + dg_off), n, loops ? 1 : 0}};
+    rc = enqueue(d, dp, jobs, (Job*)(base + job_off), nullptr, (int*)(base + cnt_off), nullptr, 0, st,
+                 (const uint64_t*)(base + mk_off), (double*)(base + tm_off));
+    if (rc) return rc;
+    std::vector<double> tmp((size_t)count * 2);
+    HAF_CUDA(cudaMemcpyAsync(tmp.data(), base + tm_off, (size_t)count * 16, cudaMemcpyDeviceToHost, st));
+    HAF_CUDA(cudaStreamSynchronize(st));
+    for (int64_t q = 0; q < count; ++q) {
+      res[2 * perm[q]] = tmp[2 * q];
+      res[2 * perm[q] + 1] = tmp[2 * q + 1];
+    }
+  }
+  std::memcpy(terms, res.data(), res.size() * sizeof(double));
+  return HAF_OK;
+}
+
+int haf_fp64_peak(double* tflops, double* ms_out) {
+  if (!tflops) return fail(HAF_EINVAL, "haf_fp64_peak: null pointer");
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device* d;
+  int rc = get_device(&d);
+  if (rc) return rc;
+  const int blocks = d->sms * 4, threads = 256, iters = 2000;
+  double* sink = nullptr;
+  HAF_CUDA(cudaMalloc(&sink, (size_t)blocks * threads * sizeof(double)));
+  cudaEvent_t e0, e1;
+  HAF_CUDA(cudaEventCreate(&e0));
+  HAF_CUDA(cudaEventCreate(&e1));
+  HAF_CUDA(launch_fp64_probe(sink, 10, blocks, d->stream));
+  HAF_CUDA(cudaEventRecord(e0, d->stream));
+  HAF_CUDA(launch_fp64_probe(sink, iters, blocks, d->stream));
+  HAF_CUDA(cudaEventRecord(e1, d->stream));
+  HAF_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  HAF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  const double flops = 2.0 * 4.0 * 16.0 * iters * (double)blocks * threads;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  if (ms_out) *ms_out = ms;
+  return HAF_OK;
+}
+
+const char* haf_last_error(void) { return g_last_error.c_str(); }
+const char* haf_version(void) { return "hafnian_gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// haf_internal.h -- structures shared by the host planner (haf_capi.cu) and
+// the device kernels (haf_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace hafgb {
+
+// One matrix of a launch.
+struct Job {
+  const double* At;    // device, n*n scalars: At[i*n+j] = A[i^1][j] (X A), 0 where j == i^1
+  const double* diag;  // device, n scalars: diag(A) (loop weights)
+  int n;               // even, >= 2
+  int loops;           // 1: loop hafnian summand
+};
+
+// A contiguous range of colex-ordered subsets of one size m of one job.
+// Subsets are bitmasks over the h = n/2 pairs; `mask0` is the first one
+// (or, in per-term mode, `rank0` indexes the caller's mask list).
+struct Chunk {
+  uint64_t mask0;
+  uint64_t rank0;
+  uint32_t count;  // subsets in the chunk
+  uint16_t job;
+  uint8_t m;       // |Z|; the tile is N = 2m square
+  uint8_t G;       // lanes per subset (1,2,4,8,16,32); 32/G subsets per warp
+  uint8_t ld;      // tile leading dimension (N or N+1)
+  uint8_t pad[7];
+};
+static_assert(sizeof(Chunk) == 32, "Chunk layout");
+
+struct KernelArgs {
+  const Job* jobs;
+  const Chunk* chunks;
+  const int* order;        // scheduling order (LPT): chunk ids
+  int nchunks;
+  int* counter;            // work counter, zeroed before the launch
+  double* partials;        // 5 doubles per chunk: re_hi, re_lo, im_hi, im_lo, abs
+  const double* tables;    // [0..127] k/2, [128..255] 1/k (1/0 := 0)
+  const uint64_t* masks;   // per-term mode: subset list (else null)
+  double* terms_out;       // per-term mode: 2 doubles per subset (else null)
+  int warp_bytes;          // shared-memory bytes owned by each warp
+};
+
+constexpr int kWarpsPerBlock = 4;
+constexpr int kMaxSmemPerBlock = 232448;  // 227 KiB opt-in on sm_100/sm_103
+constexpr int kWarpBytes = (kMaxSmemPerBlock / kWarpsPerBlock) / 16 * 16;
+constexpr int kMaxN = 56;
+
+// Shared-memory bytes one subset needs: tile N x ld, five length-N vectors,
+// six length-(h+1) series and h pair indices.
+inline __host__ __device__ int subset_bytes(int N, int ld, int h, int elem_bytes) {
+  int elems = N * ld + 5 * N + 6 * (h + 1);
+  int b = elems * elem_bytes + 4 * h;
+  return (b + 15) & ~15;
+}
+
+// Launchers (haf_kernels.cu).
+cudaError_t launch_prep(const double* A, int n, int is_real, double* At, double* diag,
+                        cudaStream_t st);
+cudaError_t launch_subsets(const KernelArgs& a, int is_real, int grid, cudaStream_t st);
+cudaError_t launch_finalize(const double* partials, const int* job_begin, int njobs, double* out,
+                            cudaStream_t st);
+cudaError_t launch_fp64_probe(double* sink, int iters, int blocks, cudaStream_t st);
+cudaError_t configure_kernels();
+
+}  // namespace hafgb

@@ -1,0 +1,48 @@
+"""Write tests/golden/oracle_values.json: oracle values for the seeded
+parity cases too slow to recompute inside the GPU test run.
+
+Every number in the file comes from ``oracle`` (the binary128 CPU oracle)
+applied to inputs from ``paper_1805_12498_gb300.inputs``; nothing here calls
+the CUDA library.
+
+    python tests/golden/make_golden.py
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle  # noqa: E402
+from paper_1805_12498_gb300 import inputs  # noqa: E402
+
+CASES = [
+    # (name, n, seed, loops, real)
+    ("cgauss28_haf", 28, 28, False, False),
+    ("cgauss28_lhaf", 28, 28, True, False),
+    ("rgauss28_haf", 28, 128, False, True),
+    ("rgauss28_lhaf", 28, 128, True, True),
+    ("cgauss32_haf", 32, 32, False, False),
+]
+
+
+def main():
+    out = {"source": "oracle.haf_formula (binary128), inputs.complex_gaussian_symmetric / "
+                     "inputs.real_gaussian_symmetric with the listed seeds",
+           "cases": []}
+    for name, n, seed, loops, real in CASES:
+        A = (inputs.real_gaussian_symmetric(n, seed) if real
+             else inputs.complex_gaussian_symmetric(n, seed))
+        t = time.time()
+        v, s = oracle.haf_formula(A, loops)
+        out["cases"].append({"name": name, "n": n, "seed": seed, "loops": loops, "real": real,
+                             "re": v.real, "im": v.imag, "abs_sum": s})
+        print(name, v, s, f"{time.time() - t:.1f}s", flush=True)
+    with open(os.path.join(HERE, "oracle_values.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()
