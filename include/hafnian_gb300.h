@@ -116,6 +116,33 @@ int haf_launch(const double* dA, int64_t n, uint32_t flags, double* d_out, void*
                size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free form of haf_launch.  The paper has no counterpart: this
+ * is a deployment variant for callers that may not allocate device memory
+ * when they ask for a hafnian -- code running under a caching allocator or
+ * memory pool that owns the device's memory, callbacks and plug-ins that may
+ * not call cudaMalloc/cudaFree (both synchronise the whole device), and
+ * services that must not grow their device footprint after start-up.
+ *
+ * It computes the same value as haf_launch (same kernels; the subset sum is
+ * chunked differently, so the last bits can differ) and calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Its scratch lives in one static
+ * device array of HAF_NOALLOC_SCRATCH_BYTES, which every GPU that loads the
+ * library holds until the process exits.
+ *   dA    : device pointer, n*n complex128 (float64 with HAF_FLAG_REAL)
+ *   d_out : device pointer to 5 doubles {re_hi, im_hi, re_lo, im_lo, abs_sum}
+ *   stream: cudaStream_t (NULL = legacy default stream); the call enqueues
+ *           work and returns before the result is ready.
+ * n must be even with 2 <= n <= HAF_MAX_N; anything else returns HAF_EINVAL
+ * with a message.  The first call on a device looks up the array's device
+ * address and sets kernel attributes; make that first call before any stream
+ * capture.  All calls share the one array: calls whose work overlaps on the
+ * GPU (e.g. on two unordered streams) race and corrupt each other's results,
+ * so order them on one stream or synchronise between them.
+ * ---------------------------------------------------------------------- */
+#define HAF_NOALLOC_SCRATCH_BYTES (1u << 20)
+int haf_launch_noalloc(const double* dA, int64_t n, uint32_t flags, double* d_out, void* stream);
+
+/* ------------------------------------------------------------------------
  * Per-subset summands (for sampling checks at large n).
  *   masks[i] : subset Z as a bitmask over the n/2 pairs (bit p <=> pair
  *              (2p, 2p+1) in Z); host array of `count` entries.

@@ -682,3 +682,165 @@ const char* haf_last_error(void) { return g_last_error.c_str(); }
 const char* haf_version(void) { return "hafnian_gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point (haf_launch_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they want a
+// hafnian: code that runs under a caching allocator or memory pool that
+// owns every byte of the device, plug-ins and callbacks that may not call
+// cudaMalloc/cudaFree (which synchronise the device), and services that
+// must not grow their footprint after start-up.  This path therefore keeps
+// all of its scratch -- the pair-swapped copy of A, the work plan, the
+// per-chunk partial sums and the work counter -- in one file-scope device
+// array of fixed size, reserved when the library is loaded and held by every
+// GPU that loads it until the process exits.
+//
+// The array is shared by every call: a call overwrites what the previous one
+// left, and clears the work counter itself before its kernels run.  Two calls
+// that overlap on the GPU (different streams without ordering between them)
+// race on the array and give wrong results; serialise them.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = HAF_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HAF_NOALLOC_SCRATCH_BYTES];
+
+// Fixed layout inside the array.
+constexpr size_t kNaCounter = 0;
+constexpr size_t kNaTables = 256;                               // 256 doubles
+constexpr size_t kNaJobs = kNaTables + 256 * sizeof(double);    // one Job
+constexpr size_t kNaAt = kNaJobs + 256;                         // n*n*16 <= 56*56*16
+constexpr size_t kNaDiag = kNaAt + (size_t)kMaxN * kMaxN * 16;  // n*16
+constexpr size_t kNaJobBegin = kNaDiag + 1024;                 // 2 ints (diag: n*16 <= 896)
+constexpr size_t kNaChunks = kNaJobBegin + 256;
+constexpr size_t kNaPerChunk = sizeof(Chunk) + sizeof(int) + 5 * sizeof(double);
+constexpr int kNaMaxChunks = (int)((kNoAllocBytes - kNaChunks) / kNaPerChunk) / 8 * 8;
+static_assert(kNaChunks % 256 == 0, "no-alloc layout alignment");
+static_assert(kNaMaxChunks >= 4096, "no-alloc scratch too small for the chunk budget");
+
+struct NoAllocDevice {
+  bool ready = false;
+  unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch
+  int sms = 0;
+};
+std::mutex g_na_mu;
+NoAllocDevice g_na_dev[64];
+
+// Host-side plan storage (static: this path allocates nothing, host or device).
+Chunk g_na_chunks[kNaMaxChunks];
+int g_na_order[kNaMaxChunks];
+double g_na_tables[256];
+
+// Per-device set-up: the device address of the array (the host-side name
+// g_noalloc_scratch is only a stand-in for it) and the kernel attributes.
+int noalloc_setup(int dev, NoAllocDevice** out) {
+  if (dev < 0 || dev >= 64) return fail(HAF_EINVAL, "haf_launch_noalloc: device ordinal out of range");
+  NoAllocDevice& d = g_na_dev[dev];
+  if (!d.ready) {
+    void* ptr = nullptr;
+    HAF_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    HAF_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+    HAF_CUDA(configure_kernels());
+    for (int k = 0; k < 128; ++k) g_na_tables[k] = 0.5 * k;
+    g_na_tables[128] = 0.0;
+    for (int k = 1; k < 128; ++k) g_na_tables[128 + k] = 1.0 / k;
+    d.scratch = (unsigned char*)ptr;
+    d.ready = true;
+  }
+  *out = &d;
+  return HAF_OK;
+}
+
+// Work plan for one matrix written into the static host arrays: sizes m = h
+// down to 1 (largest tiles first), each cut into chunks of roughly equal
+// work, at most kNaMaxChunks in total.  Returns the chunk count or < 0.
+int noalloc_plan(int n, int is_real, int num_warps) {
+  const int h = n / 2, elem = is_real ? 8 : 16;
+  double total = 0.0;
+  for (int m = 1; m <= h; ++m) total += (double)binom(h, m) * std::pow(2.0 * m, 3);
+  int per_warp = 8;
+  for (;;) {
+    const double target = std::max(1.0, total / (double)(num_warps * per_warp));
+    int nc = 0;
+    bool over = false;
+    for (int m = h; m >= 1 && !over; --m) {
+      const int N = 2 * m;
+      SizeCfg cfg;
+      if (!choose_cfg(N, h, elem, &cfg)) return fail(HAF_EINVAL, "haf_launch_noalloc: n too large");
+      const int S = 32 / cfg.G;
+      const uint64_t cnt = binom(h, m);
+      uint64_t csz = (uint64_t)std::ceil(target / std::pow((double)N, 3) / S) * S;
+      csz = std::min<uint64_t>(std::max<uint64_t>(csz, (uint64_t)S), (uint64_t)1 << 30);
+      for (uint64_t r0 = 0; r0 < cnt; r0 += csz) {
+        if (nc >= kNaMaxChunks) {
+          over = true;
+          break;
+        }
+        Chunk& c = g_na_chunks[nc];
+        std::memset(&c, 0, sizeof(c));
+        c.rank0 = r0;
+        c.mask0 = unrank_colex(r0, m, h);
+        c.count = (uint32_t)std::min<uint64_t>(csz, cnt - r0);
+        c.m = (uint8_t)m;
+        c.G = (uint8_t)cfg.G;
+        c.ld = (uint8_t)cfg.ld;
+        g_na_order[nc] = nc;
+        ++nc;
+      }
+    }
+    if (!over) return nc;
+    if (per_warp == 1) return fail(HAF_EINVAL, "haf_launch_noalloc: plan exceeds the scratch array");
+    per_warp /= 2;
+  }
+}
+
+}  // namespace
+
+extern "C" int haf_launch_noalloc(const double* dA, int64_t n, uint32_t flags, double* d_out, void* stream) {
+  if (n < 2 || n > kMaxN || (n & 1))
+    return fail(HAF_EINVAL, "haf_launch_noalloc: n must be even and 2 <= n <= HAF_MAX_N (56)");
+  if (!dA || !d_out) return fail(HAF_EINVAL, "haf_launch_noalloc: null pointer");
+  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL)) return fail(HAF_EINVAL, "haf_launch_noalloc: unknown flags");
+  const int loops = (flags & HAF_FLAG_LOOPS) ? 1 : 0, is_real = (flags & HAF_FLAG_REAL) ? 1 : 0;
+  std::lock_guard<std::mutex> lk(g_na_mu);
+  int dev = 0;
+  HAF_CUDA(cudaGetDevice(&dev));
+  NoAllocDevice* d;
+  int rc = noalloc_setup(dev, &d);
+  if (rc) return rc;
+  const int nc = noalloc_plan((int)n, is_real, d->sms * kWarpsPerBlock);
+  if (nc < 0) return nc;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* s = d->scratch;
+  Chunk* chunks = (Chunk*)(s + kNaChunks);
+  int* order = (int*)(s + kNaChunks + (size_t)kNaMaxChunks * sizeof(Chunk));
+  double* partials = (double*)(s + kNaChunks + (size_t)kNaMaxChunks * (sizeof(Chunk) + sizeof(int)));
+  int* job_begin = (int*)(s + kNaJobBegin);
+  const int jb[2] = {0, nc};
+  double* At = (double*)(s + kNaAt);
+  double* diag = (double*)(s + kNaDiag);
+  const Job job{At, diag, (int)n, loops};
+  HAF_CUDA(cudaMemcpyAsync(s + kNaTables, g_na_tables, sizeof(g_na_tables), cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemcpyAsync(s + kNaJobs, &job, sizeof(Job), cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemcpyAsync(job_begin, jb, sizeof(jb), cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemcpyAsync(chunks, g_na_chunks, (size_t)nc * sizeof(Chunk), cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemcpyAsync(order, g_na_order, (size_t)nc * sizeof(int), cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemsetAsync(s + kNaCounter, 0, sizeof(int), st));
+  HAF_CUDA(launch_prep(dA, (int)n, is_real, At, diag, st));
+  KernelArgs a;
+  a.jobs = (const Job*)(s + kNaJobs);
+  a.chunks = chunks;
+  a.order = order;
+  a.nchunks = nc;
+  a.counter = (int*)(s + kNaCounter);
+  a.partials = partials;
+  a.tables = (const double*)(s + kNaTables);
+  a.masks = nullptr;
+  a.terms_out = nullptr;
+  a.warp_bytes = kWarpBytes;
+  const int grid = std::max(1, std::min(d->sms, (nc + kWarpsPerBlock - 1) / kWarpsPerBlock));
+  HAF_CUDA(launch_subsets(a, is_real, grid, st));
+  HAF_CUDA(launch_finalize(partials, job_begin, 1, d_out, st));
+  return HAF_OK;
+}
