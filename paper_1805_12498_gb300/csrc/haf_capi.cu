@@ -656,7 +656,7 @@ int haf_fp64_peak(double* tflops, double* ms_out) {
   Device* d;
   int rc = get_device(&d);
   if (rc) return rc;
-  const int blocks = d->sms * 4, threads = 256, iters = 2000;
+  const int blocks = d->sms, threads = 512, iters = 2000;
   double* sink = nullptr;
   HAF_CUDA(cudaMalloc(&sink, (size_t)blocks * threads * sizeof(double)));
   cudaEvent_t e0, e1;
@@ -672,7 +672,7 @@ int haf_fp64_peak(double* tflops, double* ms_out) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(sink);
-  const double flops = 2.0 * 4.0 * 16.0 * iters * (double)blocks * threads;
+  const double flops = 2.0 * 8.0 * 16.0 * iters * (double)blocks * threads;
   *tflops = flops / (ms * 1e-3) / 1e12;
   if (ms_out) *ms_out = ms;
   return HAF_OK;

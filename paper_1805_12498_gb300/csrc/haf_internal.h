@@ -43,7 +43,10 @@ struct KernelArgs {
   int warp_bytes;          // shared-memory bytes owned by each warp
 };
 
-constexpr int kWarpsPerBlock = 4;
+#ifndef HAF_WARPS_PER_BLOCK
+#define HAF_WARPS_PER_BLOCK 4
+#endif
+constexpr int kWarpsPerBlock = HAF_WARPS_PER_BLOCK;
 constexpr int kMaxSmemPerBlock = 232448;  // 227 KiB opt-in on sm_100/sm_103
 constexpr int kWarpBytes = (kMaxSmemPerBlock / kWarpsPerBlock) / 16 * 16;
 constexpr int kMaxN = 56;

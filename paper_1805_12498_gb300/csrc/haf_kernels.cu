@@ -230,11 +230,210 @@ __device__ __forceinline__ uint64_t next_comb(uint64_t x) {
 }
 
 // ---------------------------------------------------------------------------
+// Row- and column-blocked pieces of a Householder step.  A G-lane group
+// spreads a row range [lo, hi) over its lanes (lane g takes rows
+// lo + g, lo + g + G, ...) and walks the columns once for up to four of its
+// rows at a time, so each shared-memory load of a broadcast vector entry
+// feeds several independent complex FMAs.  Rows past `hi` are clamped to a
+// valid row for the loads and never stored.
+// ---------------------------------------------------------------------------
+constexpr int kBlk = 4;
+
+// P[i] = sum_{j=k1}^{N-1} A_ij W[j] for NR rows starting at i0 (stride G).
+template <class T, int NR>
+__device__ __forceinline__ void rows_matvec(const T* __restrict__ tile, int ld, int k1, int N, int i0,
+                                            int hi, int G, const T* __restrict__ W, T* __restrict__ P) {
+  using O = Ops<T>;
+  const T* rp[NR];
+  T acc[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int i = i0 + r * G;
+    rp[r] = tile + (i < hi ? i : hi - 1) * ld;
+    acc[r] = O::zero();
+  }
+  for (int j = k1; j < N; ++j) {
+    const T w = W[j];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = O::fma(rp[r][j], w, acc[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int i = i0 + r * G;
+    if (i < hi) P[i] = acc[r];
+  }
+}
+
+// A_ij -= P[i] conj(W[j])  (+ W[i] TV[j] when TWO) for j in [k1, N), NR rows from i0.
+template <class T, int NR, bool TWO>
+__device__ __forceinline__ void rows_update(T* __restrict__ tile, int ld, int k1, int N, int i0, int hi,
+                                            int G, const T* __restrict__ W, const T* __restrict__ TV,
+                                            const T* __restrict__ P) {
+  using O = Ops<T>;
+  T* rp[NR];
+  T pr[NR], wr[NR];
+  bool ok[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int i = i0 + r * G;
+    ok[r] = i < hi;
+    const int ic = ok[r] ? i : hi - 1;
+    rp[r] = tile + ic * ld;
+    pr[r] = P[ic];
+    wr[r] = TWO ? W[ic] : O::zero();
+  }
+  for (int j = k1; j < N; ++j) {
+    const T w = W[j];
+    const T t = TWO ? TV[j] : O::zero();
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      T a = rp[r][j];
+      a = O::fnma_cb(pr[r], w, a);
+      if (TWO) a = O::fnma(wr[r], t, a);
+      if (ok[r]) rp[r][j] = a;
+    }
+  }
+}
+
+// TV[j] = sum_{i=k1}^{N-1} conj(W[i]) A_ij - gam conj(W[j]) for NC columns from j0 (stride G).
+template <class T, int NC>
+__device__ __forceinline__ void cols_sum(const T* __restrict__ tile, int ld, int k1, int jhi, int j0, int G,
+                                         const T* __restrict__ W, T gam, T* __restrict__ TV, int N) {
+  using O = Ops<T>;
+  int jc[NC];
+  T acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int j = j0 + c * G;
+    jc[c] = j < jhi ? j : jhi - 1;
+    acc[c] = O::zero();
+  }
+  for (int i = k1; i < N; ++i) {
+    const T w = W[i];
+    const T* row = tile + i * ld;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = O::cfma(w, row[jc[c]], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int j = j0 + c * G;
+    if (j < jhi) TV[j] = O::fnma_cb(gam, W[j], acc[c]);
+  }
+}
+
+// Rows [lo, hi): the first floor((hi-lo)/G) row slots give every lane a row
+// (register-blocked, four rows per column walk); the remaining rows (fewer
+// than G) are split by columns so that every lane gets an equal share.
+template <class T>
+__device__ __forceinline__ void range_matvec(const T* tile, int ld, int k1, int N, int lo, int hi, int g, int G,
+                                             const T* W, T* P, T* X) {
+  using O = Ops<T>;
+  const int full = (hi - lo) / G;
+  const int hb = lo + full * G;
+  for (int r0 = 0; r0 < full; r0 += kBlk) {
+    const int i0 = lo + g + r0 * G;
+    switch (min(kBlk, full - r0)) {
+      case 4: rows_matvec<T, 4>(tile, ld, k1, N, i0, hb, G, W, P); break;
+      case 3: rows_matvec<T, 3>(tile, ld, k1, N, i0, hb, G, W, P); break;
+      case 2: rows_matvec<T, 2>(tile, ld, k1, N, i0, hb, G, W, P); break;
+      default: rows_matvec<T, 1>(tile, ld, k1, N, i0, hb, G, W, P); break;
+    }
+  }
+  const int rem = hi - hb;
+  if (rem > 0) {
+    // lane g: remainder row q = g % rem, column chunk c = g / rem of nc chunks
+    const int nc = G / rem;
+    const int q = g % rem, c = g / rem;
+    T acc = O::zero();
+    if (c < nc) {
+      const T* row = tile + (hb + q) * ld;
+      for (int j = k1 + c; j < N; j += nc) acc = O::fma(row[j], W[j], acc);
+    }
+    X[g] = acc;
+    __syncwarp();
+    if (g < rem) {
+      T sum = X[g];
+      for (int cc = 1; cc < nc; ++cc) sum = O::add(sum, X[g + cc * rem]);
+      P[hb + g] = sum;
+    }
+  }
+}
+
+template <class T, bool TWO>
+__device__ __forceinline__ void range_update(T* tile, int ld, int k1, int N, int lo, int hi, int g, int G,
+                                             const T* W, const T* TV, const T* P) {
+  using O = Ops<T>;
+  const int full = (hi - lo) / G;
+  const int hb = lo + full * G;
+  for (int r0 = 0; r0 < full; r0 += kBlk) {
+    const int i0 = lo + g + r0 * G;
+    switch (min(kBlk, full - r0)) {
+      case 4: rows_update<T, 4, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
+      case 3: rows_update<T, 3, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
+      case 2: rows_update<T, 2, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
+      default: rows_update<T, 1, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
+    }
+  }
+  // remainder rows [hb, hi): elements (i, j) spread round-robin over the lanes
+  const int L = N - k1;
+  const int E = (hi - hb) * L;
+  int ii = hb, j = k1 + g;
+  while (j >= N && ii < hi) {
+    j -= L;
+    ++ii;
+  }
+  for (int e = g; e < E; e += G) {
+    T* a = tile + ii * ld + j;
+    T v = O::fnma_cb(P[ii], W[j], *a);
+    if (TWO) v = O::fnma(W[ii], TV[j], v);
+    *a = v;
+    j += G;
+    while (j >= N && ii < hi) {
+      j -= L;
+      ++ii;
+    }
+  }
+}
+
+// Columns [k1, N): full column slots blocked, the remaining columns (fewer
+// than G) split by rows with the partial sums combined through X.
+template <class T>
+__device__ __forceinline__ void range_colsum(const T* tile, int ld, int k1, int N, int g, int G, const T* W,
+                                             T gam, T* TV, T* X) {
+  using O = Ops<T>;
+  const int full = (N - k1) / G;
+  const int jb = k1 + full * G;
+  for (int c0 = 0; c0 < full; c0 += kBlk) {
+    const int j0 = k1 + g + c0 * G;
+    switch (min(kBlk, full - c0)) {
+      case 4: cols_sum<T, 4>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
+      case 3: cols_sum<T, 3>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
+      case 2: cols_sum<T, 2>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
+      default: cols_sum<T, 1>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
+    }
+  }
+  const int rem = N - jb;
+  if (rem > 0) {
+    const int nc = G / rem;
+    const int q = g % rem, c = g / rem;
+    T acc = O::zero();
+    if (c < nc)
+      for (int i = k1 + c; i < N; i += nc) acc = O::cfma(W[i], tile[i * ld + jb + q], acc);
+    X[g] = acc;
+    __syncwarp();
+    if (g < rem) {
+      T sum = X[g];
+      for (int cc = 1; cc < nc; ++cc) sum = O::add(sum, X[g + cc * rem]);
+      TV[jb + g] = O::fnma_cb(gam, W[jb + g], sum);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Householder reduction to upper Hessenberg form, in place, by one G-lane
-// group.  Lane g owns rows (and, for the column sums, columns) i = g mod G.
-// Step k reflects rows/columns K = {k+1, ..., N-1}:
-//   w from column k; p = A[:,K] w; s_j = sum_{i in K} conj(w_i) A_ij;
-//   gamma = w^H p_K; t_j = s_j - gamma conj(w_j);
+// group.  Step k reflects rows/columns K = {k+1, ..., N-1}:
+//   w from column k; p = A[:,K] w; gamma = w^H p_K;
+//   t_j = sum_{i in K} conj(w_i) A_ij - gamma conj(w_j);
 //   A_ij -= p_i conj(w_j) (all rows) and -= w_i t_j (rows in K),
 // which is A <- (I - w w^H) A (I - w w^H) restricted to the active block.
 // With `loops`, va <- va (I - w w^H) and vb <- (I - w w^H) vb as well.
@@ -242,11 +441,11 @@ __device__ __forceinline__ uint64_t next_comb(uint64_t x) {
 template <class T>
 __device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__ W,
                             T* __restrict__ P, T* __restrict__ TV, T* __restrict__ VA,
-                            T* __restrict__ VB, bool loops, int g, int G) {
+                            T* __restrict__ VB, T* __restrict__ X, bool loops, int g, int G) {
   using O = Ops<T>;
   for (int k = 0; k + 2 < N; ++k) {
     const int k1 = k + 1;
-    const int i2 = first_owned(k + 2, g, G);
+    const int i2 = k + 2 + g;  // this lane's rows below the first reflected entry
     double sig = 0.0;
     for (int i = i2; i < N; i += G) sig = O::abs2_acc(tile[i * ld + k], sig);
     sig = group_sum(sig, G);
@@ -256,58 +455,34 @@ __device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__
     T w0, alpha;
     O::reflector(x0, s0, s0 + sig, c, w0, alpha);
     for (int i = i2; i < N; i += G) W[i] = O::scale(tile[i * ld + k], c);
-    if ((k1 & (G - 1)) == g) {
+    if (g == 0) {
       W[k1] = w0;
       tile[k1 * ld + k] = alpha;
     }
     __syncwarp();
-    // p = A[:, K] w, all rows.
-    for (int i = g; i < N; i += G) {
-      const T* row = tile + i * ld;
-      T acc = O::zero();
-      for (int j = k1; j < N; ++j) acc = O::fma(row[j], W[j], acc);
-      P[i] = acc;
-    }
-    const int i1 = first_owned(k1, g, G);
+    range_matvec<T>(tile, ld, k1, N, 0, N, g, G, W, P, X);  // p = A[:, K] w
+    __syncwarp();
     T gam = O::zero();
-    for (int i = i1; i < N; i += G) gam = O::cfma(W[i], P[i], gam);
+    for (int i = k1 + g; i < N; i += G) gam = O::cfma(W[i], P[i], gam);
     gam = group_sum_t(gam, G);
-    // s_j for owned columns j in K, then t_j.
-    for (int j = i1; j < N; j += G) {
-      T acc = O::zero();
-      for (int i = k1; i < N; ++i) acc = O::cfma(W[i], tile[i * ld + j], acc);
-      TV[j] = O::fnma_cb(gam, W[j], acc);
-    }
+    __syncwarp();
+    range_colsum<T>(tile, ld, k1, N, g, G, W, gam, TV, X);  // t_j
     if (loops) {
       T aw = O::zero(), wb = O::zero();
-      for (int i = i1; i < N; i += G) {
+      for (int i = k1 + g; i < N; i += G) {
         aw = O::fma(VA[i], W[i], aw);
         wb = O::cfma(W[i], VB[i], wb);
       }
       aw = group_sum_t(aw, G);
       wb = group_sum_t(wb, G);
-      for (int i = i1; i < N; i += G) {
+      for (int i = k1 + g; i < N; i += G) {
         VA[i] = O::fnma_cb(aw, W[i], VA[i]);
         VB[i] = O::fnma(W[i], wb, VB[i]);
       }
     }
     __syncwarp();
-    // Rank-2 update of the active columns.
-    for (int i = g; i < N; i += G) {
-      T* row = tile + i * ld;
-      const T pi = P[i];
-      if (i >= k1) {
-        const T wi = W[i];
-        for (int j = k1; j < N; ++j) {
-          T a = row[j];
-          a = O::fnma_cb(pi, W[j], a);
-          a = O::fnma(wi, TV[j], a);
-          row[j] = a;
-        }
-      } else {
-        for (int j = k1; j < N; ++j) row[j] = O::fnma_cb(pi, W[j], row[j]);
-      }
-    }
+    range_update<T, false>(tile, ld, k1, N, 0, k1, g, G, W, TV, P);  // rows above K
+    range_update<T, true>(tile, ld, k1, N, k1, N, g, G, W, TV, P);   // rows in K
     __syncwarp();
   }
 }
@@ -358,14 +533,25 @@ __device__ void loop_moments(const T* __restrict__ tile, int ld, int N, int h,
 //         - sum_{m=1}^{i-1} c_{i,m} lambda^{m+1} D_{i-1-m},
 //   c_{i,m} = H_{i-1-m, i-1} prod_{l=i-m}^{i-1} H_{l, l-1}.
 // The products are folded into the upper triangle first (column by column,
-// from the diagonal upward).  D_r[1..min(r,h)] for r < N are kept in row r
-// of the tile, columns 0..r-1 (free after the reduction: below-subdiagonal
-// entries and, once folded, the subdiagonal); D_N goes to DN.
+// from the diagonal upward), so c_{i,m} = H'_{i-1-m, i-1}.
+// The sum is evaluated "right-looking": once D_r is final, its terms
+//   D_{r+1}[j]   += D_r[j] - alpha_r D_r[j-1]
+//   D_i[t+i-r]   -= H'_{r, i-1} D_r[t]          (i = r+2..N)
+// are added to every later polynomial; the (i, t) pairs of one r are spread
+// evenly over the group's lanes.  D_i[1..min(i,h)] for i < N accumulate in
+// row i of the tile, columns 0..i-1 (free after the reduction: entries
+// below the subdiagonal and, once folded, the subdiagonal); D_N goes to DN.
 // ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T* dslot(T* tile, int ld, int N, T* DN, int i, int j) {
+  return (i < N) ? tile + i * ld + (j - 1) : DN + j;
+}
+
 template <class T>
 __device__ void labudde(T* __restrict__ tile, int ld, int N, int h, T* __restrict__ DN, int g,
                         int G) {
   using O = Ops<T>;
+  // fold the subdiagonal products into the upper triangle
   for (int b = (g == 0 ? G : g); b < N; b += G) {
     T rho = tile[b * ld + b - 1];
     tile[(b - 1) * ld + b] = O::mul(tile[(b - 1) * ld + b], rho);
@@ -375,26 +561,62 @@ __device__ void labudde(T* __restrict__ tile, int ld, int N, int h, T* __restric
     }
   }
   __syncwarp();
+  // zero the accumulators D_i[1..min(i,h)], i = 1..N
   for (int i = 1; i <= N; ++i) {
     const int J = min(i, h);
-    const T alpha = tile[(i - 1) * ld + (i - 1)];
-    const T* prev = tile + (i - 1) * ld;  // D_{i-1}[j] at prev[j-1] (i-1 >= 1)
-    T* dst = (i < N) ? tile + i * ld - 1 : DN;  // D_i[j] at dst[j]
-    for (int q = 0; q * G < J; ++q) {
-      const int t = q * G + ((q & 1) ? (G - 1 - g) : g);
-      if (t >= J) continue;
-      const int j = t + 1;
-      // D_{i-1}[j] - alpha D_{i-1}[j-1]
-      T acc = (i >= 2 && j <= i - 1) ? prev[j - 1] : O::zero();
-      const T dm1 = (j == 1) ? O::one() : prev[j - 2];
-      acc = O::fnma(alpha, dm1, acc);
-      // m = 1..j-2: c_{i,m} D_{i-1-m}[j-m-1], both in row r = i-1-m
-      for (int m = 1; m <= j - 2; ++m) {
-        const T* row = tile + (i - 1 - m) * ld;
-        acc = O::fnma(row[i - 1], row[j - m - 2], acc);
+    for (int j = 1 + g; j <= J; j += G) *dslot(tile, ld, N, DN, i, j) = O::zero();
+  }
+  __syncwarp();
+  for (int r = 0; r < N; ++r) {
+    const T alpha = tile[r * ld + r];
+    const T* Dr = tile + r * ld - 1;  // D_r[t] = Dr[t] for 1 <= t <= min(r,h)
+    const T* Hr = tile + r * ld;      // H'_{r, i-1} = Hr[i-1]
+    const int Ja = min(r + 1, h);     // part (a): j = 1..Ja of D_{r+1}
+    // part (b): rows i = r+2..N, t = 0..min(r, h-(i-r)); rectangle then triangle
+    const int ra = min(r, h);
+    int Eb = 0;
+    for (int i = r + 2; i <= N; ++i) {
+      const int cnt = min(ra, h - (i - r)) + 1;
+      if (cnt <= 0) break;
+      Eb += cnt;
+    }
+    const int E = Ja + Eb;
+    // walk this lane's elements e = g, g+G, ...; (i, t) is the position
+    // inside part (b), advanced row by row (at most N rows per walk)
+    int e = g, i = r + 2, t = 0;
+    auto walk = [&]() {
+      while (i <= N) {
+        const int cnt = min(ra, h - (i - r)) + 1;
+        if (cnt <= 0 || t < cnt) break;
+        t -= cnt;
+        ++i;
       }
-      if (j >= 2) acc = O::sub(acc, tile[(i - j) * ld + (i - 1)]);
-      dst[j] = acc;
+    };
+    if (e >= Ja) {
+      t = e - Ja;
+      walk();
+    }
+    for (; e < E; e += G) {
+      if (e < Ja) {
+        const int j = e + 1;
+        const T d = (j <= r) ? Dr[j] : O::zero();
+        const T dm = (j == 1) ? O::one() : Dr[j - 1];
+        T* a = dslot(tile, ld, N, DN, r + 1, j);
+        *a = O::fnma(alpha, dm, O::add(*a, d));
+      } else {
+        const T d = (t == 0) ? O::one() : Dr[t];
+        T* a = dslot(tile, ld, N, DN, i, t + i - r);
+        *a = O::fnma(Hr[i - 1], d, *a);
+      }
+      if (e + G >= Ja) {
+        if (e < Ja) {
+          t = e + G - Ja;
+          i = r + 2;
+        } else {
+          t += G;
+        }
+        walk();
+      }
     }
     __syncwarp();
   }
@@ -526,7 +748,7 @@ __device__ void process_chunk(const KernelArgs& args, const Chunk& ch, int chunk
       }
     }
     __syncwarp();
-    householder<T>(tile, ld, N, W, P, TV, VA, VB, loops, g, G);
+    householder<T>(tile, ld, N, W, P, TV, VA, VB, DN, loops, g, G);  // DN area as scratch
     if (loops) loop_moments<T>(tile, ld, N, h, VA, VB, W, TV, U, g, G);
     labudde<T>(tile, ld, N, h, DN, g, G);
     if (loops && N < h) loop_moments_tail<T>(N, h, DN, U, g, G);
@@ -653,19 +875,23 @@ __global__ void finalize_kernel(const double* __restrict__ partials, const int* 
 }
 
 // Dependent DFMA chains over every SM: the FP64 roofline denominator.
-__global__ void __launch_bounds__(256) fp64_probe_kernel(double* sink, int iters) {
-  double a0 = 1.0 + 1e-3 * threadIdx.x, a1 = a0 + 1e-4, a2 = a0 + 2e-4, a3 = a0 + 3e-4;
-  const double b = 0.9999999, c = 1e-7;
+// Eight independent chains per thread with operands in registers (b and c
+// arrive as kernel arguments), 16 warps per SM.
+__global__ void __launch_bounds__(512) fp64_probe_kernel(double* sink, int iters, double b, double c) {
+  double a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = 1.0 + 1e-3 * (threadIdx.x + i);
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-      a0 = ::fma(a0, b, c);
-      a1 = ::fma(a1, b, c);
-      a2 = ::fma(a2, b, c);
-      a3 = ::fma(a3, b, c);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = ::fma(a[i], b, c);
     }
   }
-  sink[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3;
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += a[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 }  // namespace
@@ -705,7 +931,7 @@ cudaError_t launch_finalize(const double* partials, const int* job_begin, int nj
 }
 
 cudaError_t launch_fp64_probe(double* sink, int iters, int blocks, cudaStream_t st) {
-  fp64_probe_kernel<<<blocks, 256, 0, st>>>(sink, iters);
+  fp64_probe_kernel<<<blocks, 512, 0, st>>>(sink, iters, 0.9999999, 1e-7);
   return cudaGetLastError();
 }
 
