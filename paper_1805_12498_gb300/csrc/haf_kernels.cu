@@ -237,7 +237,16 @@ __device__ __forceinline__ uint64_t next_comb(uint64_t x) {
 // feeds several independent complex FMAs.  Rows past `hi` are clamped to a
 // valid row for the loads and never stored.
 // ---------------------------------------------------------------------------
-constexpr int kBlk = 4;
+#ifndef HAF_KBLK
+#define HAF_KBLK 4
+#endif
+#ifndef HAF_JUNROLL
+#define HAF_JUNROLL 1
+#endif
+#define HAF_STR_(x) #x
+#define HAF_STR(x) HAF_STR_(x)
+#define HAF_UNROLL_J _Pragma(HAF_STR(unroll HAF_JUNROLL))
+constexpr int kBlk = HAF_KBLK;
 
 // P[i] = sum_{j=k1}^{N-1} A_ij W[j] for NR rows starting at i0 (stride G).
 template <class T, int NR>
@@ -252,6 +261,7 @@ __device__ __forceinline__ void rows_matvec(const T* __restrict__ tile, int ld, 
     rp[r] = tile + (i < hi ? i : hi - 1) * ld;
     acc[r] = O::zero();
   }
+  HAF_UNROLL_J
   for (int j = k1; j < N; ++j) {
     const T w = W[j];
 #pragma unroll
@@ -282,6 +292,7 @@ __device__ __forceinline__ void rows_update(T* __restrict__ tile, int ld, int k1
     pr[r] = P[ic];
     wr[r] = TWO ? W[ic] : O::zero();
   }
+  HAF_UNROLL_J
   for (int j = k1; j < N; ++j) {
     const T w = W[j];
     const T t = TWO ? TV[j] : O::zero();
@@ -308,6 +319,7 @@ __device__ __forceinline__ void cols_sum(const T* __restrict__ tile, int ld, int
     jc[c] = j < jhi ? j : jhi - 1;
     acc[c] = O::zero();
   }
+  HAF_UNROLL_J
   for (int i = k1; i < N; ++i) {
     const T w = W[i];
     const T* row = tile + i * ld;
@@ -333,6 +345,12 @@ __device__ __forceinline__ void range_matvec(const T* tile, int ld, int k1, int 
   for (int r0 = 0; r0 < full; r0 += kBlk) {
     const int i0 = lo + g + r0 * G;
     switch (min(kBlk, full - r0)) {
+#if HAF_KBLK > 4
+      case 8: rows_matvec<T, 8>(tile, ld, k1, N, i0, hb, G, W, P); break;
+      case 7: rows_matvec<T, 7>(tile, ld, k1, N, i0, hb, G, W, P); break;
+      case 6: rows_matvec<T, 6>(tile, ld, k1, N, i0, hb, G, W, P); break;
+      case 5: rows_matvec<T, 5>(tile, ld, k1, N, i0, hb, G, W, P); break;
+#endif
       case 4: rows_matvec<T, 4>(tile, ld, k1, N, i0, hb, G, W, P); break;
       case 3: rows_matvec<T, 3>(tile, ld, k1, N, i0, hb, G, W, P); break;
       case 2: rows_matvec<T, 2>(tile, ld, k1, N, i0, hb, G, W, P); break;
@@ -368,6 +386,12 @@ __device__ __forceinline__ void range_update(T* tile, int ld, int k1, int N, int
   for (int r0 = 0; r0 < full; r0 += kBlk) {
     const int i0 = lo + g + r0 * G;
     switch (min(kBlk, full - r0)) {
+#if HAF_KBLK > 4
+      case 8: rows_update<T, 8, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
+      case 7: rows_update<T, 7, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
+      case 6: rows_update<T, 6, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
+      case 5: rows_update<T, 5, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
+#endif
       case 4: rows_update<T, 4, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
       case 3: rows_update<T, 3, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
       case 2: rows_update<T, 2, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
@@ -406,6 +430,12 @@ __device__ __forceinline__ void range_colsum(const T* tile, int ld, int k1, int 
   for (int c0 = 0; c0 < full; c0 += kBlk) {
     const int j0 = k1 + g + c0 * G;
     switch (min(kBlk, full - c0)) {
+#if HAF_KBLK > 4
+      case 8: cols_sum<T, 8>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
+      case 7: cols_sum<T, 7>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
+      case 6: cols_sum<T, 6>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
+      case 5: cols_sum<T, 5>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
+#endif
       case 4: cols_sum<T, 4>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
       case 3: cols_sum<T, 3>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
       case 2: cols_sum<T, 2>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
@@ -509,7 +539,10 @@ __device__ void loop_moments(const T* __restrict__ tile, int ld, int N, int h,
   for (int k = 2; k <= kmax; ++k) {
     __syncwarp();
     T uk = O::zero();
-    for (int i = g; i < N; i += G) {
+    // rows in zig-zag order over the lanes (row i has N - i + 1 entries)
+    for (int q = 0; q * G < N; ++q) {
+      const int i = q * G + ((q & 1) ? (G - 1 - g) : g);
+      if (i >= N) continue;
       const T* row = tile + i * ld;
       T acc = O::zero();
       for (int j = (i > 0 ? i - 1 : 0); j < N; ++j) acc = O::fma(row[j], Y0[j], acc);
@@ -571,51 +604,39 @@ __device__ void labudde(T* __restrict__ tile, int ld, int N, int h, T* __restric
     const T alpha = tile[r * ld + r];
     const T* Dr = tile + r * ld - 1;  // D_r[t] = Dr[t] for 1 <= t <= min(r,h)
     const T* Hr = tile + r * ld;      // H'_{r, i-1} = Hr[i-1]
-    const int Ja = min(r + 1, h);     // part (a): j = 1..Ja of D_{r+1}
-    // part (b): rows i = r+2..N, t = 0..min(r, h-(i-r)); rectangle then triangle
+    // (a) D_{r+1}[j] += D_r[j] - alpha_r D_r[j-1], j = 1..min(r+1,h); lanes over j
+    const int Ja = min(r + 1, h);
+    for (int j = 1 + g; j <= Ja; j += G) {
+      const T d = (j <= r) ? Dr[j] : O::zero();
+      const T dm = (j == 1) ? O::one() : Dr[j - 1];
+      T* a = dslot(tile, ld, N, DN, r + 1, j);
+      *a = O::fnma(alpha, dm, O::add(*a, d));
+    }
+    // (b) D_i[t+i-r] -= H'_{r,i-1} D_r[t] for rows i = r+2..imax and
+    //     t = 0..min(ra, h-(i-r)).  Lanes form a Gi x Gt grid over (row, t),
+    //     with the split chosen per r to balance rows against coefficients.
     const int ra = min(r, h);
-    int Eb = 0;
-    for (int i = r + 2; i <= N; ++i) {
-      const int cnt = min(ra, h - (i - r)) + 1;
-      if (cnt <= 0) break;
-      Eb += cnt;
-    }
-    const int E = Ja + Eb;
-    // walk this lane's elements e = g, g+G, ...; (i, t) is the position
-    // inside part (b), advanced row by row (at most N rows per walk)
-    int e = g, i = r + 2, t = 0;
-    auto walk = [&]() {
-      while (i <= N) {
-        const int cnt = min(ra, h - (i - r)) + 1;
-        if (cnt <= 0 || t < cnt) break;
-        t -= cnt;
-        ++i;
-      }
-    };
-    if (e >= Ja) {
-      t = e - Ja;
-      walk();
-    }
-    for (; e < E; e += G) {
-      if (e < Ja) {
-        const int j = e + 1;
-        const T d = (j <= r) ? Dr[j] : O::zero();
-        const T dm = (j == 1) ? O::one() : Dr[j - 1];
-        T* a = dslot(tile, ld, N, DN, r + 1, j);
-        *a = O::fnma(alpha, dm, O::add(*a, d));
-      } else {
-        const T d = (t == 0) ? O::one() : Dr[t];
-        T* a = dslot(tile, ld, N, DN, i, t + i - r);
-        *a = O::fnma(Hr[i - 1], d, *a);
-      }
-      if (e + G >= Ja) {
-        if (e < Ja) {
-          t = e + G - Ja;
-          i = r + 2;
-        } else {
-          t += G;
+    const int imax = min(N, h + r);
+    const int nrows = imax - (r + 1);
+    if (nrows > 0) {
+      int Gi = 1, best = 1 << 30;
+      for (int gi = 1; gi <= G; gi <<= 1) {
+        const int cost = ((nrows + gi - 1) / gi) * ((ra + 1 + (G / gi) - 1) / (G / gi));
+        if (cost < best) {
+          best = cost;
+          Gi = gi;
         }
-        walk();
+      }
+      const int Gt = G / Gi;
+      const int gi = g & (Gi - 1), gt = g / Gi;
+      for (int i = r + 2 + gi; i <= imax; i += Gi) {
+        const T hri = Hr[i - 1];
+        const int tmax = min(ra, h - (i - r));
+        T* a = dslot(tile, ld, N, DN, i, i - r);  // D_i[t + i - r] = a[t]
+        for (int t = gt; t <= tmax; t += Gt) {
+          const T d = (t == 0) ? O::one() : Dr[t];
+          a[t] = O::fnma(hri, d, a[t]);
+        }
       }
     }
     __syncwarp();
