@@ -99,6 +99,28 @@ int lhaf_c128_batched(const double* const* As, const int64_t* ns, int64_t count,
                       haf_info* infos);
 
 /* ------------------------------------------------------------------------
+ * Sharding one matrix over several GPUs or processes (the subset sum splits
+ * into independent ranges with one final sum, Sec. 4.1).  Part p of P takes,
+ * for every subset size m, the p-th of P contiguous, nearly equal slices of
+ * the colex-ordered m-subsets; the slices depend only on (n, p, P), so
+ * processes on different machines agree on them.
+ *   haf_part        : A on the host (complex128, or float64 with HAF_FLAG_REAL;
+ *                     HAF_FLAG_LOOPS for lhaf); writes the part's record
+ *                     rec[5] = {re_hi, im_hi, re_lo, im_lo, abs_sum}.  Runs
+ *                     on the calling thread's current CUDA device.
+ *   haf_part_subsets: number of subset terms part p evaluates (host only).
+ *   haf_combine     : host-only fixed-order double-double sum of `nparts`
+ *                     records (recs[5*nparts]) into out[5]; the value is
+ *                     (out[0] + out[2]) + i (out[1] + out[3]).
+ * n = 0 and odd n follow the whole-matrix conventions (value in part 0).
+ * Returns HAF_EINVAL unless 0 <= part < nparts.
+ * ---------------------------------------------------------------------- */
+int haf_part(const double* A, int64_t n, uint32_t flags, int64_t part, int64_t nparts, double* rec,
+             haf_info* info);
+int haf_part_subsets(int64_t n, int64_t part, int64_t nparts, int64_t* subsets);
+int haf_combine(const double* recs, int64_t nparts, double* out);
+
+/* ------------------------------------------------------------------------
  * Device-resident asynchronous form (for callers that own device memory and
  * streams, e.g. through PyTorch).
  *   dA        : device pointer, n*n complex128 (or float64 with HAF_FLAG_REAL)

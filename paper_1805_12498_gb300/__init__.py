@@ -22,7 +22,7 @@ from . import _native
 from ._native import HAF_FLAG_LOOPS, HAF_FLAG_REAL, HAF_MAX_N, HafError  # noqa: F401
 
 __all__ = ["haf", "lhaf", "haf_info", "haf_batched", "haf_terms", "workspace_bytes",
-           "haf_launch", "fp64_peak", "HafError", "HAF_MAX_N"]
+           "haf_launch", "haf_part", "part_subsets", "combine", "fp64_peak", "HafError", "HAF_MAX_N"]
 
 
 @dataclass
@@ -115,6 +115,38 @@ def haf_launch(dA_ptr: int, n: int, d_out_ptr: int, d_work_ptr: int, ws_bytes: i
     d_out_ptr when the stream reaches it."""
     flags = (HAF_FLAG_LOOPS if loops else 0) | (HAF_FLAG_REAL if real else 0)
     _native.check(_native.lib().haf_launch(dA_ptr, n, flags, d_out_ptr, d_work_ptr, ws_bytes, stream_ptr))
+
+
+def haf_part(A, part: int, nparts: int, loops: bool = False, real: bool | None = None) -> np.ndarray:
+    """Record {re_hi, im_hi, re_lo, im_lo, abs_sum} of part `part` of `nparts`
+    of the subset sum (each size class cut into nparts contiguous slices);
+    runs on the current CUDA device.  Combine the parts with ``combine``."""
+    if real is None:
+        real = not np.iscomplexobj(A)
+    A = _prep(A, real)
+    flags = (HAF_FLAG_LOOPS if loops else 0) | (HAF_FLAG_REAL if real else 0)
+    rec = np.zeros(5)
+    info = _native.HafInfo()
+    _native.check(_native.lib().haf_part(A.ctypes.data_as(_native._DP), A.shape[0], flags, part, nparts,
+                                         rec.ctypes.data_as(_native._DP), ctypes.byref(info)))
+    return rec
+
+
+def part_subsets(n: int, part: int, nparts: int) -> int:
+    """Number of subset terms that part `part` of `nparts` evaluates (host only)."""
+    out = ctypes.c_int64()
+    _native.check(_native.lib().haf_part_subsets(n, part, nparts, ctypes.byref(out)))
+    return out.value
+
+
+def combine(records) -> tuple[complex, float]:
+    """Fixed-order double-double sum of part records (host only):
+    returns (value, abs_sum)."""
+    recs = np.ascontiguousarray(np.asarray(records, dtype=np.float64).reshape(-1, 5))
+    out = np.zeros(5)
+    _native.check(_native.lib().haf_combine(recs.ctypes.data_as(_native._DP), recs.shape[0],
+                                            out.ctypes.data_as(_native._DP)))
+    return complex(out[0] + out[2], out[1] + out[3]), float(out[4])
 
 
 def fp64_peak() -> tuple[float, float]:

@@ -74,6 +74,13 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         L.haf_launch.restype = ctypes.c_int
         L.haf_terms_c128.argtypes = [_DP, ctypes.c_int64, ctypes.c_int, _U64P, ctypes.c_int64, _DP]
         L.haf_terms_c128.restype = ctypes.c_int
+        L.haf_part.argtypes = [_DP, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, _DP,
+                               ctypes.POINTER(HafInfo)]
+        L.haf_part.restype = ctypes.c_int
+        L.haf_part_subsets.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _I64P]
+        L.haf_part_subsets.restype = ctypes.c_int
+        L.haf_combine.argtypes = [_DP, ctypes.c_int64, _DP]
+        L.haf_combine.restype = ctypes.c_int
         L.haf_fp64_peak.argtypes = [_DP, _DP]
         L.haf_fp64_peak.restype = ctypes.c_int
         L.haf_last_error.argtypes = []

@@ -88,7 +88,18 @@ struct JobSpec {
   int n;
   int loops;
   int is_real;
+  int64_t part = 0;    // this job covers part `part` of `nparts` of every size class
+  int64_t nparts = 1;
 };
+
+// Colex rank range [lo, hi) of the m-subsets that part p of P covers: each
+// size class is cut into P contiguous, nearly equal pieces, so the parts
+// are balanced and depend on nothing but (h, m, p, P).
+void part_range(uint64_t cnt, int64_t p, int64_t P, uint64_t* lo, uint64_t* hi) {
+  const unsigned __int128 c = cnt;
+  *lo = (uint64_t)(c * (unsigned __int128)p / (unsigned __int128)P);
+  *hi = (uint64_t)(c * (unsigned __int128)(p + 1) / (unsigned __int128)P);
+}
 
 struct Plan {
   std::vector<Chunk> chunks;
@@ -105,7 +116,7 @@ int build_plan(const std::vector<JobSpec>& jobs, int num_warps, Plan* plan) {
   double total = 0.0;
   for (const JobSpec& js : jobs) {
     const int h = js.n / 2;
-    for (int m = 1; m <= h; ++m) total += (double)binom(h, m) * std::pow(2.0 * m, 3);
+    for (int m = 1; m <= h; ++m) total += (double)binom(h, m) * std::pow(2.0 * m, 3) / (double)js.nparts;
   }
   const double target = std::max(1.0, total / (double)(num_warps * 8));
   std::vector<double> cost;
@@ -118,7 +129,9 @@ int build_plan(const std::vector<JobSpec>& jobs, int num_warps, Plan* plan) {
       SizeCfg cfg;
       if (!choose_cfg(N, h, elem, &cfg)) return fail(HAF_EINVAL, "matrix too large for the shared-memory plan");
       const int S = 32 / cfg.G;
-      const uint64_t cnt = binom(h, m);
+      uint64_t rlo, rhi;
+      part_range(binom(h, m), js.part, js.nparts, &rlo, &rhi);
+      const uint64_t cnt = rhi - rlo;
       const double per = std::pow((double)N, 3);
       uint64_t csz = (uint64_t)std::ceil(target / per / S) * S;
       csz = std::max<uint64_t>(csz, (uint64_t)S);
@@ -126,8 +139,8 @@ int build_plan(const std::vector<JobSpec>& jobs, int num_warps, Plan* plan) {
       for (uint64_t r0 = 0; r0 < cnt; r0 += csz) {
         Chunk c;
         std::memset(&c, 0, sizeof(c));
-        c.rank0 = r0;
-        c.mask0 = unrank_colex(r0, m, h);
+        c.rank0 = rlo + r0;
+        c.mask0 = unrank_colex(rlo + r0, m, h);
         c.count = (uint32_t)std::min<uint64_t>(csz, cnt - r0);
         c.job = (uint16_t)jb;
         c.m = (uint8_t)m;
@@ -170,7 +183,7 @@ struct Device {
   size_t work_bytes = 0;
   double* host_out = nullptr;  // pinned, grows
   size_t host_out_n = 0;
-  std::map<std::tuple<int, int, int>, DevPlan> plans;  // (n, loops, real) -> plan
+  std::map<std::tuple<int, int, int, int64_t, int64_t>, DevPlan> plans;  // (n, loops, real, part, nparts)
 };
 
 std::mutex g_mu;
@@ -223,15 +236,19 @@ void free_plan(DevPlan* dp) {
   *dp = DevPlan();
 }
 
-int cached_plan(Device* d, int n, int loops, int is_real, DevPlan** out) {
-  auto key = std::make_tuple(n, loops, is_real);
+int cached_plan(Device* d, int n, int loops, int is_real, DevPlan** out, int64_t part = 0,
+                int64_t nparts = 1) {
+  auto key = std::make_tuple(n, loops, is_real, part, nparts);
   auto it = d->plans.find(key);
   if (it != d->plans.end()) {
     *out = &it->second;
     return HAF_OK;
   }
   Plan p;
-  int rc = build_plan({JobSpec{n, loops, is_real}}, d->sms * kWarpsPerBlock, &p);
+  JobSpec js{n, loops, is_real};
+  js.part = part;
+  js.nparts = nparts;
+  int rc = build_plan({js}, d->sms * kWarpsPerBlock, &p);
   if (rc) return rc;
   DevPlan dp;
   rc = upload_plan(p, d->stream, &dp);
@@ -384,6 +401,74 @@ int run_single(const double* A, int64_t n64, int loops, int is_real, double* out
   return HAF_OK;
 }
 
+// Part `part` of `nparts` of the subset sum of one matrix (host pointers,
+// synchronous): writes the raw record {re_hi, im_hi, re_lo, im_lo, abs_sum}
+// of that part's signed terms.  n = 0 and odd n follow the conventions of
+// the whole-matrix entry points (the value goes to part 0).
+int run_part(const double* A, int64_t n64, int loops, int is_real, int64_t part, int64_t nparts,
+             double* rec, haf_info* info) {
+  const double t0 = now_s();
+  if (n64 < 0 || n64 > kMaxN) return fail(HAF_EINVAL, "n out of range");
+  if (nparts < 1 || part < 0 || part >= nparts) return fail(HAF_EINVAL, "part must satisfy 0 <= part < nparts");
+  if (!rec || (n64 > 0 && !A)) return fail(HAF_EINVAL, "null pointer");
+  int n = (int)n64;
+  const int elem = is_real ? 1 : 2;
+  auto trivial = [&](double v) {
+    rec[0] = (part == 0) ? v : 0.0;
+    rec[1] = rec[2] = rec[3] = 0.0;
+    rec[4] = (part == 0) ? std::fabs(v) : 0.0;
+    if (info) *info = haf_info{rec[4], {0.0, 0.0}, 0, now_s() - t0, 0};
+    return HAF_OK;
+  };
+  if (n == 0) return trivial(1.0);
+  std::vector<double> padded;
+  if (n & 1) {
+    if (!loops) return trivial(0.0);
+    const int np = n + 1;
+    if (np > kMaxN) return fail(HAF_EINVAL, "n out of range");
+    padded.assign((size_t)np * np * elem, 0.0);
+    for (int i = 0; i < n; ++i)
+      std::memcpy(&padded[(size_t)i * np * elem], A + (size_t)i * n * elem, (size_t)n * elem * sizeof(double));
+    padded[((size_t)n * np + n) * elem] = 1.0;
+    A = padded.data();
+    n = np;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device* d;
+  int rc = get_device(&d);
+  if (rc) return rc;
+  DevPlan* dp;
+  rc = cached_plan(d, n, loops, is_real, &dp, part, nparts);
+  if (rc) return rc;
+  WsLayout w = ws_layout(n, dp->nchunks);
+  const size_t jobs_off = w.total, out_off = jobs_off + 256, stage_off = out_off + 256;
+  const size_t abytes = (size_t)n * n * elem * sizeof(double);
+  rc = ensure_work(d, stage_off + align256(abytes));
+  if (rc) return rc;
+  rc = ensure_host_out(d, 5);
+  if (rc) return rc;
+  char* base = (char*)d->work;
+  double* At = (double*)(base + w.at);
+  double* diag = (double*)(base + w.diag);
+  double* Ad = (double*)(base + stage_off);
+  cudaStream_t st = d->stream;
+  HAF_CUDA(cudaMemcpyAsync(Ad, A, abytes, cudaMemcpyHostToDevice, st));
+  HAF_CUDA(launch_prep(Ad, n, is_real, At, diag, st));
+  if (dp->nchunks == 0) {
+    rec[0] = rec[1] = rec[2] = rec[3] = rec[4] = 0.0;
+  } else {
+    std::vector<Job> jobs{Job{At, diag, n, loops}};
+    rc = enqueue(d, *dp, jobs, (Job*)(base + jobs_off), (double*)(base + w.partials), (int*)(base + w.counter),
+                 (double*)(base + out_off), is_real, st);
+    if (rc) return rc;
+    HAF_CUDA(cudaMemcpyAsync(d->host_out, base + out_off, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HAF_CUDA(cudaStreamSynchronize(st));
+    std::memcpy(rec, d->host_out, 5 * sizeof(double));
+  }
+  if (info) *info = haf_info{rec[4], {rec[2], rec[3]}, dp->subsets, now_s() - t0, dp->nchunks ? 3 : 1};
+  return HAF_OK;
+}
+
 int run_batched(const double* const* As, const int64_t* ns, int64_t count, int loops, double* outs,
                 haf_info* infos) {
   const double t0 = now_s();
@@ -518,6 +603,52 @@ int haf_c128_batched(const double* const* As, const int64_t* ns, int64_t count, 
 }
 int lhaf_c128_batched(const double* const* As, const int64_t* ns, int64_t count, double* outs, haf_info* infos) {
   return run_batched(As, ns, count, 1, outs, infos);
+}
+
+int haf_part(const double* A, int64_t n, uint32_t flags, int64_t part, int64_t nparts, double* rec,
+             haf_info* info) {
+  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL)) return fail(HAF_EINVAL, "haf_part: unknown flags");
+  return run_part(A, n, (flags & HAF_FLAG_LOOPS) ? 1 : 0, (flags & HAF_FLAG_REAL) ? 1 : 0, part, nparts, rec, info);
+}
+
+int haf_part_subsets(int64_t n, int64_t part, int64_t nparts, int64_t* subsets) {
+  if (n < 0 || n > kMaxN || nparts < 1 || part < 0 || part >= nparts || !subsets)
+    return fail(HAF_EINVAL, "haf_part_subsets: bad arguments");
+  const int h = (int)(n / 2);
+  int64_t total = 0;
+  for (int m = 1; m <= h; ++m) {
+    uint64_t lo, hi;
+    part_range(binom(h, m), part, nparts, &lo, &hi);
+    total += (int64_t)(hi - lo);
+  }
+  *subsets = total;
+  return HAF_OK;
+}
+
+int haf_combine(const double* recs, int64_t nparts, double* out) {
+  if (nparts < 1 || !recs || !out) return fail(HAF_EINVAL, "haf_combine: bad arguments");
+  // Fixed-order double-double sum (Knuth's TwoSum, then a fast renormalisation).
+  double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0, ab = 0.0;
+  auto add = [](double& hi, double& lo, double xh, double xl) {
+    const double s = hi + xh;
+    const double bb = s - hi;
+    double e = (hi - (s - bb)) + (xh - bb);
+    e += lo + xl;
+    hi = s + e;
+    lo = e - (hi - s);
+  };
+  for (int64_t p = 0; p < nparts; ++p) {
+    const double* r = recs + 5 * p;
+    add(rh, rl, r[0], r[2]);
+    add(ih, il, r[1], r[3]);
+    ab += r[4];
+  }
+  out[0] = rh;
+  out[1] = ih;
+  out[2] = rl;
+  out[3] = il;
+  out[4] = ab;
+  return HAF_OK;
 }
 
 size_t haf_workspace_bytes(int64_t n, uint32_t flags) {
