@@ -469,73 +469,75 @@ int run_part(const double* A, int64_t n64, int loops, int is_real, int64_t part,
   return HAF_OK;
 }
 
-int run_batched(const double* const* As, const int64_t* ns, int64_t count, int loops, double* outs,
-                haf_info* infos) {
-  const double t0 = now_s();
-  if (count < 0 || (count > 0 && (!As || !ns || !outs))) return fail(HAF_EINVAL, "null pointer");
-  if (count > 65535) return fail(HAF_EINVAL, "batch too large (max 65535 matrices per call)");
+// ---------------------------------------------------------------------------
+// Batch engine: many matrices of mixed sizes in one persistent launch.
+// A batch's plan (chunks of every matrix, largest tiles first), its device
+// buffers and a CUDA graph of the whole sequence -- one host-to-device copy
+// from pinned staging, one prep launch for all matrices, the subset kernel,
+// the finalize kernel and one device-to-host copy -- are built once per
+// list of sizes and replayed while the sizes repeat.
+// ---------------------------------------------------------------------------
+struct BatchPlan {
+  std::vector<int> ns;  // sizes after padding (all even, >= 2)
+  int loops = -1;
+  int is_real = 0;
+  char* dbuf = nullptr;
+  double* h_in = nullptr;   // pinned staging of the inputs
+  double* h_out = nullptr;  // pinned results, 5 per job
+  std::vector<size_t> in_off;  // per job offset in h_in (doubles)
+  size_t in_doubles = 0;
+  int64_t subsets = 0;
+  int nchunks = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+
+void free_batch(BatchPlan* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->dbuf) cudaFree(b->dbuf);
+  if (b->h_in) cudaFreeHost(b->h_in);
+  if (b->h_out) cudaFreeHost(b->h_out);
+  *b = BatchPlan();
+}
+
+std::map<int, BatchPlan> g_batch;  // device -> last batch plan
+
+int build_batch(Device* d, const std::vector<int>& ns, int loops, int is_real, BatchPlan* b) {
+  free_batch(b);
+  b->ns = ns;
+  b->loops = loops;
+  b->is_real = is_real;
+  const int njobs = (int)ns.size();
   std::vector<JobSpec> specs;
-  std::vector<int64_t> idx;  // job -> batch index
-  std::vector<std::vector<double>> pads;
-  std::vector<const double*> srcs;
-  for (int64_t b = 0; b < count; ++b) {
-    int64_t n = ns[b];
-    if (n < 0 || n > kMaxN || (n > 0 && !As[b])) return fail(HAF_EINVAL, "bad matrix in batch");
-  }
-  for (int64_t b = 0; b < count; ++b) {
-    int n = (int)ns[b];
-    const double* A = As[b];
-    if (n == 0) {
-      outs[2 * b] = 1.0;
-      outs[2 * b + 1] = 0.0;
-      if (infos) infos[b] = haf_info{1.0, {0.0, 0.0}, 0, 0.0, 0};
-      continue;
-    }
-    if (n & 1) {
-      if (!loops) {
-        outs[2 * b] = 0.0;
-        outs[2 * b + 1] = 0.0;
-        if (infos) infos[b] = haf_info{0.0, {0.0, 0.0}, 0, 0.0, 0};
-        continue;
-      }
-      const int np = n + 1;
-      if (np > kMaxN) return fail(HAF_EINVAL, "n out of range");
-      std::vector<double> p((size_t)np * np * 2, 0.0);
-      for (int i = 0; i < n; ++i) std::memcpy(&p[(size_t)i * np * 2], A + (size_t)i * n * 2, (size_t)n * 2 * sizeof(double));
-      p[((size_t)n * np + n) * 2] = 1.0;
-      pads.push_back(std::move(p));
-      A = pads.back().data();
-      n = np;
-    }
-    specs.push_back(JobSpec{n, loops, 0});
-    idx.push_back(b);
-    srcs.push_back(A);
-  }
-  if (specs.empty()) return HAF_OK;
-  std::lock_guard<std::mutex> lk(g_mu);
-  Device* d;
-  int rc = get_device(&d);
-  if (rc) return rc;
+  for (int n : ns) specs.push_back(JobSpec{n, loops, is_real});
   Plan p;
-  rc = build_plan(specs, d->sms * kWarpsPerBlock, &p);
+  int rc = build_plan(specs, d->sms * kWarpsPerBlock, &p);
   if (rc) return rc;
-  const int njobs = (int)specs.size();
-  // layout: per job A (staging), At, diag; then jobs, partials, counter, out, plan arrays
-  std::vector<size_t> a_off(njobs), at_off(njobs), dg_off(njobs);
+  b->subsets = p.subsets;
+  b->nchunks = (int)p.chunks.size();
+  const size_t elem = is_real ? 8 : 16;
+  // device layout
   size_t off = 0;
+  std::vector<size_t> in_off(njobs), at_off(njobs), dg_off(njobs);
+  size_t in_doubles = 0;
   for (int j = 0; j < njobs; ++j) {
-    const size_t nn = (size_t)specs[j].n * specs[j].n * 16;
-    a_off[j] = off;
-    off += align256(nn);
+    const size_t nn = (size_t)ns[j] * ns[j];
+    in_off[j] = in_doubles;
+    in_doubles += (nn * elem / 8 + 31) / 32 * 32;  // 256-byte aligned per job
+  }
+  const size_t din_off = off;
+  off += align256(in_doubles * 8);
+  for (int j = 0; j < njobs; ++j) {
     at_off[j] = off;
-    off += align256(nn);
+    off += align256((size_t)ns[j] * ns[j] * elem);
     dg_off[j] = off;
-    off += align256((size_t)specs[j].n * 16);
+    off += align256((size_t)ns[j] * elem);
   }
   const size_t jobs_off = off;
-  off += align256(njobs * sizeof(Job));
+  off += align256((size_t)njobs * sizeof(Job));
+  const size_t srcs_off = off;
+  off += align256((size_t)njobs * sizeof(double*));
   const size_t part_off = off;
-  off += align256(p.chunks.size() * 5 * sizeof(double));
+  off += align256((size_t)std::max(1, b->nchunks) * 5 * sizeof(double));
   const size_t cnt_off = off;
   off += 256;
   const size_t out_off = off;
@@ -546,44 +548,116 @@ int run_batched(const double* const* As, const int64_t* ns, int64_t count, int l
   off += align256(p.order.size() * sizeof(int));
   const size_t jb_off = off;
   off += align256(p.job_begin.size() * sizeof(int));
-  rc = ensure_work(d, off);
-  if (rc) return rc;
-  rc = ensure_host_out(d, (size_t)njobs * 5);
-  if (rc) return rc;
-  char* base = (char*)d->work;
-  cudaStream_t st = d->stream;
+  cudaError_t e = cudaMalloc(&b->dbuf, off);
+  if (e != cudaSuccess) return fail(HAF_ENOMEM, std::string("batch buffers: ") + cudaGetErrorString(e));
+  HAF_CUDA(cudaMallocHost(&b->h_in, std::max<size_t>(1, in_doubles) * 8));
+  HAF_CUDA(cudaMallocHost(&b->h_out, (size_t)njobs * 5 * sizeof(double)));
+  b->in_off = in_off;
+  b->in_doubles = in_doubles;
+  char* base = b->dbuf;
   std::vector<Job> jobs(njobs);
+  std::vector<const double*> srcs(njobs);
   for (int j = 0; j < njobs; ++j) {
-    const int n = specs[j].n;
-    HAF_CUDA(cudaMemcpyAsync(base + a_off[j], srcs[j], (size_t)n * n * 16, cudaMemcpyHostToDevice, st));
-    HAF_CUDA(launch_prep((double*)(base + a_off[j]), n, 0, (double*)(base + at_off[j]),
-                         (double*)(base + dg_off[j]), st));
-    jobs[j] = Job{(double*)(base + at_off[j]), (double*)(base + dg_off[j]), n, loops};
+    jobs[j] = Job{(double*)(base + at_off[j]), (double*)(base + dg_off[j]), ns[j], loops};
+    srcs[j] = (const double*)(base + din_off) + in_off[j];
   }
-  DevPlan dp;
-  dp.chunks = (Chunk*)(base + ch_off);
-  dp.order = (int*)(base + ord_off);
-  dp.job_begin = (int*)(base + jb_off);
-  dp.nchunks = (int)p.chunks.size();
-  dp.njobs = njobs;
-  dp.subsets = p.subsets;
-  HAF_CUDA(cudaMemcpyAsync(dp.chunks, p.chunks.data(), p.chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice, st));
-  HAF_CUDA(cudaMemcpyAsync(dp.order, p.order.data(), p.order.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-  HAF_CUDA(cudaMemcpyAsync(dp.job_begin, p.job_begin.data(), p.job_begin.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-  rc = enqueue(d, dp, jobs, (Job*)(base + jobs_off), (double*)(base + part_off), (int*)(base + cnt_off),
-               (double*)(base + out_off), 0, st);
-  if (rc) return rc;
-  HAF_CUDA(cudaMemcpyAsync(d->host_out, base + out_off, (size_t)njobs * 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  cudaStream_t st = d->stream;
+  HAF_CUDA(cudaMemcpyAsync(base + jobs_off, jobs.data(), njobs * sizeof(Job), cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemcpyAsync(base + srcs_off, srcs.data(), njobs * sizeof(double*), cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemcpyAsync(base + ch_off, p.chunks.data(), p.chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemcpyAsync(base + ord_off, p.order.data(), p.order.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  HAF_CUDA(cudaMemcpyAsync(base + jb_off, p.job_begin.data(), p.job_begin.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   HAF_CUDA(cudaStreamSynchronize(st));
+  // capture the per-batch sequence once
+  KernelArgs a;
+  a.jobs = (const Job*)(base + jobs_off);
+  a.chunks = (const Chunk*)(base + ch_off);
+  a.order = (const int*)(base + ord_off);
+  a.nchunks = b->nchunks;
+  a.counter = (int*)(base + cnt_off);
+  a.partials = (double*)(base + part_off);
+  a.tables = d->tables;
+  a.masks = nullptr;
+  a.terms_out = nullptr;
+  a.warp_bytes = kWarpBytes;
+  const int grid = std::max(1, std::min(d->sms, (b->nchunks + kWarpsPerBlock - 1) / kWarpsPerBlock));
+  cudaGraph_t graph;
+  HAF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t ce = cudaMemcpyAsync(base + din_off, b->h_in, in_doubles * 8, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = launch_prep_batch((const double* const*)(base + srcs_off), a.jobs, njobs, is_real, st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+  if (ce == cudaSuccess) ce = launch_subsets(a, is_real, grid, st);
+  if (ce == cudaSuccess) ce = launch_finalize(a.partials, (const int*)(base + jb_off), njobs, (double*)(base + out_off), st);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(b->h_out, base + out_off, (size_t)njobs * 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaError_t ee = cudaStreamEndCapture(st, &graph);
+  if (ce != cudaSuccess) return fail(HAF_ECUDA, std::string("batch capture: ") + cudaGetErrorString(ce));
+  if (ee != cudaSuccess) return fail(HAF_ECUDA, std::string("batch capture end: ") + cudaGetErrorString(ee));
+  ee = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ee != cudaSuccess) return fail(HAF_ECUDA, std::string("batch graph: ") + cudaGetErrorString(ee));
+  return HAF_OK;
+}
+
+int run_batched(const double* const* As, const int64_t* ns, int64_t count, int loops, double* outs,
+                haf_info* infos) {
+  const double t0 = now_s();
+  if (count < 0 || (count > 0 && (!As || !ns || !outs))) return fail(HAF_EINVAL, "null pointer");
+  if (count > 65535) return fail(HAF_EINVAL, "batch too large (max 65535 matrices per call)");
+  for (int64_t b = 0; b < count; ++b)
+    if (ns[b] < 0 || ns[b] > kMaxN || (ns[b] > 0 && !As[b])) return fail(HAF_EINVAL, "bad matrix in batch");
+  std::vector<int> sizes;
+  std::vector<int64_t> idx;  // job -> batch index
+  for (int64_t b = 0; b < count; ++b) {
+    const int n = (int)ns[b];
+    if (n == 0 || ((n & 1) && !loops)) {
+      const double v = (n == 0) ? 1.0 : 0.0;
+      outs[2 * b] = v;
+      outs[2 * b + 1] = 0.0;
+      if (infos) infos[b] = haf_info{v, {0.0, 0.0}, 0, 0.0, 0};
+      continue;
+    }
+    if (n + (n & 1) > kMaxN) return fail(HAF_EINVAL, "n out of range");
+    sizes.push_back(n + (n & 1));
+    idx.push_back(b);
+  }
+  if (sizes.empty()) return HAF_OK;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device* d;
+  int rc = get_device(&d);
+  if (rc) return rc;
+  BatchPlan& bp = g_batch[d->id];
+  if (bp.ns != sizes || bp.loops != loops || bp.is_real != 0) {
+    rc = build_batch(d, sizes, loops, 0, &bp);
+    if (rc) {
+      free_batch(&bp);
+      return rc;
+    }
+  }
+  // stage the inputs (odd lhaf matrices padded with an isolated looped vertex)
+  for (size_t j = 0; j < sizes.size(); ++j) {
+    const int64_t b = idx[j];
+    const int n = (int)ns[b], np = sizes[j];
+    double* dst = bp.h_in + bp.in_off[j];
+    if (np == n) {
+      std::memcpy(dst, As[b], (size_t)n * n * 16);
+    } else {
+      std::memset(dst, 0, (size_t)np * np * 16);
+      for (int i = 0; i < n; ++i) std::memcpy(dst + (size_t)i * np * 2, As[b] + (size_t)i * n * 2, (size_t)n * 16);
+      dst[((size_t)n * np + n) * 2] = 1.0;
+    }
+  }
+  HAF_CUDA(cudaGraphLaunch(bp.exec, d->stream));
+  HAF_CUDA(cudaStreamSynchronize(d->stream));
   const double secs = now_s() - t0;
-  for (int j = 0; j < njobs; ++j) {
-    const double* o = d->host_out + 5 * j;
+  for (size_t j = 0; j < sizes.size(); ++j) {
+    const double* o = bp.h_out + 5 * j;
     const int64_t b = idx[j];
     outs[2 * b] = o[0] + o[2];
     outs[2 * b + 1] = o[1] + o[3];
     if (infos) {
-      const int h = specs[j].n / 2;
-      infos[b] = haf_info{o[4], {o[2], o[3]}, (int64_t)((1ull << h) - 1), secs, (int64_t)(njobs + 2)};
+      const int h = sizes[j] / 2;
+      infos[b] = haf_info{o[4], {o[2], o[3]}, (int64_t)((1ull << h) - 1), secs, 5};
     }
   }
   return HAF_OK;

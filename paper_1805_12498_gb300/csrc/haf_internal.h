@@ -63,6 +63,8 @@ inline __host__ __device__ int subset_bytes(int N, int ld, int h, int elem_bytes
 cudaError_t launch_prep(const double* A, int n, int is_real, double* At, double* diag,
                         cudaStream_t st);
 cudaError_t launch_subsets(const KernelArgs& a, int is_real, int grid, cudaStream_t st);
+cudaError_t launch_prep_batch(const double* const* srcs, const Job* jobs, int njobs, int is_real,
+                              cudaStream_t st);
 cudaError_t launch_finalize(const double* partials, const int* job_begin, int njobs, double* out,
                             cudaStream_t st);
 cudaError_t launch_fp64_probe(double* sink, int iters, int blocks, cudaStream_t st);

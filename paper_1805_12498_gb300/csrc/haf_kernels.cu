@@ -849,6 +849,30 @@ __global__ void prep_kernel(const double* __restrict__ A, int n, double* __restr
   }
 }
 
+// Batched form of prep_kernel: block b prepares job b from srcs[b].
+template <class T>
+__global__ void prep_batch_kernel(const double* const* __restrict__ srcs, const Job* __restrict__ jobs) {
+  const Job jb = jobs[blockIdx.x];
+  const double* A = srcs[blockIdx.x];
+  const int n = jb.n, total = n * n;
+  double* At = const_cast<double*>(jb.At);
+  double* diag = const_cast<double*>(jb.diag);
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    const int ii = i ^ 1;
+    const int r = min(ii, j), c = max(ii, j);
+    if (sizeof(T) == 16) {
+      double2 v = make_double2(0.0, 0.0);
+      if (ii != j) v = reinterpret_cast<const double2*>(A)[(size_t)r * n + c];
+      reinterpret_cast<double2*>(At)[e] = v;
+      if (j == i) reinterpret_cast<double2*>(diag)[i] = reinterpret_cast<const double2*>(A)[(size_t)i * n + i];
+    } else {
+      At[e] = (ii != j) ? A[(size_t)r * n + c] : 0.0;
+      if (j == i) diag[i] = A[(size_t)i * n + i];
+    }
+  }
+}
+
 // Fixed-order double-double reduction of one job's chunk partials.
 __global__ void finalize_kernel(const double* __restrict__ partials, const int* __restrict__ job_begin,
                                 double* __restrict__ out) {
@@ -933,6 +957,16 @@ cudaError_t launch_prep(const double* A, int n, int is_real, double* At, double*
     prep_kernel<double><<<blocks, threads, 0, st>>>(A, n, At, diag);
   else
     prep_kernel<cplx><<<blocks, threads, 0, st>>>(A, n, At, diag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_batch(const double* const* srcs, const Job* jobs, int njobs, int is_real,
+                              cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  if (is_real)
+    prep_batch_kernel<double><<<njobs, 256, 0, st>>>(srcs, jobs);
+  else
+    prep_batch_kernel<cplx><<<njobs, 256, 0, st>>>(srcs, jobs);
   return cudaGetLastError();
 }
 
