@@ -58,6 +58,9 @@ extern "C" {
 #define HAF_EINVAL (-1)    /* bad argument (null pointer, n out of range, bad flags) */
 #define HAF_ENOMEM (-2)    /* device or host allocation failed                     */
 #define HAF_ECUDA (-3)     /* a CUDA runtime call failed                           */
+#define HAF_ETIMEDOUT (-4) /* server poll gave up before the job finished          */
+#define HAF_EBUSY (-5)     /* server refused a job (queue full)                    */
+#define HAF_ENOTFOUND (-6) /* server: unknown (or already collected) ticket        */
 #define HAF_ESMALL (-7)    /* caller-supplied workspace too small                  */
 
 /* flags */
@@ -175,6 +178,39 @@ int haf_launch_noalloc(const double* dA, int64_t n, uint32_t flags, double* d_ou
  * ---------------------------------------------------------------------- */
 int haf_terms_c128(const double* A, int64_t n, int loops, const uint64_t* masks, int64_t count,
                    double* terms);
+
+/* ------------------------------------------------------------------------
+ * Server: continuous batching of haf / lhaf requests on one GPU.
+ * The paper computes one hafnian at a time (Sec. 4.1); this is the serving
+ * form of the same summands.  Requests of mixed n are admitted while job
+ * slots and device memory allow; each admitted job's subset chunks are
+ * drained by a resident kernel together with other jobs' chunks (large-n
+ * jobs are split into chunks that interleave with small ones).  A job's
+ * result does not depend on what else ran with it (its chunking and its
+ * reduction order are fixed by the job alone).
+ *   cfg          : NULL for defaults; zero fields take their defaults.
+ *   submit       : kind 0 = haf, 1 = lhaf; A is host complex128 n x n, copied
+ *                  before return; returns a ticket.  HAF_EBUSY if the queue is
+ *                  full, HAF_ENOMEM if the job can never fit the memory limit.
+ *   poll         : waits up to timeout_us (< 0: no limit) for the ticket; out
+ *                  = 2 doubles; info->seconds = latency from submit to the
+ *                  result.  A ticket is collected once (then HAF_ENOTFOUND).
+ *   destroy      : lets in-flight work finish, then frees everything.
+ * The resident kernel's warps leave after idle_us without work and the
+ * scheduler relaunches it when work arrives; no device wait is unbounded.
+ * ---------------------------------------------------------------------- */
+typedef struct haf_server haf_server;
+typedef struct haf_server_cfg {
+  int64_t max_jobs;     /* jobs admitted at once (default 256, max 65535)      */
+  int64_t max_bytes;    /* device memory for admitted jobs (default 256 MiB)   */
+  int64_t ring_entries; /* chunk descriptors in the host ring (default 2^20)   */
+  int64_t idle_us;      /* resident kernel idles out after this (default 20 ms) */
+} haf_server_cfg;
+
+int haf_server_create(const haf_server_cfg* cfg, haf_server** out);
+int haf_server_submit(haf_server* s, int kind, const double* A, int64_t n, uint64_t* ticket);
+int haf_server_poll(haf_server* s, uint64_t ticket, double* out, haf_info* info, int64_t timeout_us);
+int haf_server_destroy(haf_server* s);
 
 /* ------------------------------------------------------------------------
  * Utilities.

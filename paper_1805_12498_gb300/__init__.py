@@ -22,7 +22,8 @@ from . import _native
 from ._native import HAF_FLAG_LOOPS, HAF_FLAG_REAL, HAF_MAX_N, HafError  # noqa: F401
 
 __all__ = ["haf", "lhaf", "haf_info", "haf_batched", "haf_terms", "workspace_bytes",
-           "haf_launch", "haf_part", "part_subsets", "combine", "fp64_peak", "HafError", "HAF_MAX_N"]
+           "haf_launch", "haf_part", "part_subsets", "combine", "Server", "fp64_peak", "HafError",
+           "HAF_MAX_N"]
 
 
 @dataclass
@@ -147,6 +148,52 @@ def combine(records) -> tuple[complex, float]:
     _native.check(_native.lib().haf_combine(recs.ctypes.data_as(_native._DP), recs.shape[0],
                                             out.ctypes.data_as(_native._DP)))
     return complex(out[0] + out[2], out[1] + out[3]), float(out[4])
+
+
+class Server:
+    """Continuous-batching hafnian server on the current GPU (C ABI
+    haf_server_*): submit haf/lhaf requests of mixed n while others run,
+    collect each result once with ``poll``."""
+
+    def __init__(self, max_jobs: int = 0, max_bytes: int = 0, ring_entries: int = 0, idle_us: int = 0):
+        self._L = _native.lib()
+        cfg = _native.ServerCfg(max_jobs, max_bytes, ring_entries, idle_us)
+        h = ctypes.c_void_p()
+        _native.check(self._L.haf_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, A, loops: bool = False) -> int:
+        A = _prep(A, False)
+        t = ctypes.c_uint64()
+        _native.check(self._L.haf_server_submit(self._h, 1 if loops else 0, A.ctypes.data_as(_native._DP),
+                                                A.shape[0], ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, timeout_s: float | None = None) -> Info:
+        out = np.zeros(2)
+        info = _native.HafInfo()
+        us = -1 if timeout_s is None else int(timeout_s * 1e6)
+        _native.check(self._L.haf_server_poll(self._h, ticket, out.ctypes.data_as(_native._DP),
+                                               ctypes.byref(info), us))
+        return Info(complex(out[0], out[1]), info.abs_sum, complex(info.value_lo[0], info.value_lo[1]),
+                    info.subsets, info.seconds, info.launches)
+
+    def close(self) -> None:
+        if self._h:
+            _native.check(self._L.haf_server_destroy(self._h))
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fp64_peak() -> tuple[float, float]:

@@ -17,6 +17,9 @@ HAF_OK = 0
 HAF_EINVAL = -1
 HAF_ENOMEM = -2
 HAF_ECUDA = -3
+HAF_ETIMEDOUT = -4
+HAF_EBUSY = -5
+HAF_ENOTFOUND = -6
 HAF_ESMALL = -7
 HAF_FLAG_LOOPS = 1
 HAF_FLAG_REAL = 2
@@ -27,6 +30,11 @@ class HafInfo(ctypes.Structure):
     _fields_ = [("abs_sum", ctypes.c_double), ("value_lo", ctypes.c_double * 2),
                 ("subsets", ctypes.c_int64), ("seconds", ctypes.c_double),
                 ("launches", ctypes.c_int64)]
+
+
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("max_jobs", ctypes.c_int64), ("max_bytes", ctypes.c_int64),
+                ("ring_entries", ctypes.c_int64), ("idle_us", ctypes.c_int64)]
 
 
 class HafError(RuntimeError):
@@ -81,6 +89,16 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         L.haf_part_subsets.restype = ctypes.c_int
         L.haf_combine.argtypes = [_DP, ctypes.c_int64, _DP]
         L.haf_combine.restype = ctypes.c_int
+        L.haf_server_create.argtypes = [ctypes.POINTER(ServerCfg), ctypes.POINTER(ctypes.c_void_p)]
+        L.haf_server_create.restype = ctypes.c_int
+        L.haf_server_submit.argtypes = [ctypes.c_void_p, ctypes.c_int, _DP, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_uint64)]
+        L.haf_server_submit.restype = ctypes.c_int
+        L.haf_server_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, _DP, ctypes.POINTER(HafInfo),
+                                      ctypes.c_int64]
+        L.haf_server_poll.restype = ctypes.c_int
+        L.haf_server_destroy.argtypes = [ctypes.c_void_p]
+        L.haf_server_destroy.restype = ctypes.c_int
         L.haf_fp64_peak.argtypes = [_DP, _DP]
         L.haf_fp64_peak.restype = ctypes.c_int
         L.haf_last_error.argtypes = []

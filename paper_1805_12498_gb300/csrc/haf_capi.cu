@@ -28,14 +28,17 @@
 
 using namespace hafgb;
 
-namespace {
-
+namespace hafgb {
 thread_local std::string g_last_error;
-
-int fail(int code, const std::string& msg) {
+int set_error(int code, const std::string& msg) {
   g_last_error = msg;
   return code;
 }
+}  // namespace hafgb
+
+namespace {
+
+int fail(int code, const std::string& msg) { return hafgb::set_error(code, msg); }
 
 #define HAF_CUDA(call)                                                                    \
   do {                                                                                    \
@@ -43,6 +46,10 @@ int fail(int code, const std::string& msg) {
     if (_e != cudaSuccess)                                                                \
       return fail(HAF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e));         \
   } while (0)
+
+}  // namespace
+
+namespace hafgb {
 
 uint64_t binom(int a, int b) {
   if (b < 0 || b > a) return 0;
@@ -84,14 +91,6 @@ bool choose_cfg(int N, int h, int elem, SizeCfg* out) {
   return false;
 }
 
-struct JobSpec {
-  int n;
-  int loops;
-  int is_real;
-  int64_t part = 0;    // this job covers part `part` of `nparts` of every size class
-  int64_t nparts = 1;
-};
-
 // Colex rank range [lo, hi) of the m-subsets that part p of P covers: each
 // size class is cut into P contiguous, nearly equal pieces, so the parts
 // are balanced and depend on nothing but (h, m, p, P).
@@ -100,13 +99,6 @@ void part_range(uint64_t cnt, int64_t p, int64_t P, uint64_t* lo, uint64_t* hi) 
   *lo = (uint64_t)(c * (unsigned __int128)p / (unsigned __int128)P);
   *hi = (uint64_t)(c * (unsigned __int128)(p + 1) / (unsigned __int128)P);
 }
-
-struct Plan {
-  std::vector<Chunk> chunks;
-  std::vector<int> order;
-  std::vector<int> job_begin;  // njobs + 1
-  int64_t subsets = 0;
-};
 
 int build_plan(const std::vector<JobSpec>& jobs, int num_warps, Plan* plan) {
   plan->chunks.clear();
@@ -159,6 +151,10 @@ int build_plan(const std::vector<JobSpec>& jobs, int num_warps, Plan* plan) {
                    [&](int a, int b) { return cost[a] > cost[b]; });
   return HAF_OK;
 }
+
+}  // namespace hafgb
+
+namespace {
 
 // Device-resident copy of a plan.
 struct DevPlan {
@@ -883,7 +879,7 @@ int haf_fp64_peak(double* tflops, double* ms_out) {
   return HAF_OK;
 }
 
-const char* haf_last_error(void) { return g_last_error.c_str(); }
+const char* haf_last_error(void) { return hafgb::g_last_error.c_str(); }
 const char* haf_version(void) { return "hafnian_gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"

@@ -5,6 +5,9 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+#include <vector>
+
 namespace hafgb {
 
 // One matrix of a launch.
@@ -26,7 +29,8 @@ struct Chunk {
   uint8_t m;       // |Z|; the tile is N = 2m square
   uint8_t G;       // lanes per subset (1,2,4,8,16,32); 32/G subsets per warp
   uint8_t ld;      // tile leading dimension (N or N+1)
-  uint8_t pad[7];
+  uint8_t pad[3];
+  uint32_t aux;    // server: index of the chunk within its job
 };
 static_assert(sizeof(Chunk) == 32, "Chunk layout");
 
@@ -47,6 +51,33 @@ struct KernelArgs {
 #define HAF_WARPS_PER_BLOCK 4
 #endif
 constexpr int kWarpsPerBlock = HAF_WARPS_PER_BLOCK;
+
+// Server: one admitted job as the device sees it (slot-indexed table in
+// device memory, written by the host before the job's chunks are published).
+struct SrvJob {
+  Job job;
+  double* partials;     // device, 5 doubles per chunk
+  unsigned int* done;   // device, completed-chunk counter (zeroed at admission)
+  double* result;       // device view of mapped host memory, 5 doubles
+  unsigned int* flag;   // device view of mapped host memory, set to `gen` when done
+  unsigned int nchunks;
+  unsigned int gen;
+};
+
+static_assert(sizeof(SrvJob) % 8 == 0, "SrvJob is moved as 64-bit words");
+
+struct ServerArgs {
+  const Chunk* ring;                  // device view of the mapped host ring
+  unsigned long long cap;             // ring entries
+  const unsigned long long* tail;     // mapped host: chunks published so far
+  unsigned long long* head;           // device: chunks claimed so far
+  unsigned long long* head_mirror;    // mapped host: a recent value of *head
+  const unsigned int* stop;           // mapped host: nonzero asks the warps to leave
+  const SrvJob* jobs;                 // device job table
+  const double* tables;
+  long long idle_ns;                  // a warp leaves after this long without work
+  int warp_bytes;
+};
 constexpr int kMaxSmemPerBlock = 232448;  // 227 KiB opt-in on sm_100/sm_103
 constexpr int kWarpBytes = (kMaxSmemPerBlock / kWarpsPerBlock) / 16 * 16;
 constexpr int kMaxN = 56;
@@ -59,6 +90,25 @@ inline __host__ __device__ int subset_bytes(int N, int ld, int h, int elem_bytes
   return (b + 15) & ~15;
 }
 
+// Host planner (haf_capi.cu).
+struct JobSpec {
+  int n;
+  int loops;
+  int is_real;
+  int64_t part = 0;  // this job covers part `part` of `nparts` of every size class
+  int64_t nparts = 1;
+};
+struct Plan {
+  std::vector<Chunk> chunks;
+  std::vector<int> order;
+  std::vector<int> job_begin;  // njobs + 1
+  int64_t subsets = 0;
+};
+uint64_t binom(int a, int b);
+uint64_t unrank_colex(uint64_t rank, int m, int h);
+int build_plan(const std::vector<JobSpec>& jobs, int num_warps, Plan* plan);
+int set_error(int code, const std::string& msg);
+
 // Launchers (haf_kernels.cu).
 cudaError_t launch_prep(const double* A, int n, int is_real, double* At, double* diag,
                         cudaStream_t st);
@@ -69,5 +119,6 @@ cudaError_t launch_finalize(const double* partials, const int* job_begin, int nj
                             cudaStream_t st);
 cudaError_t launch_fp64_probe(double* sink, int iters, int blocks, cudaStream_t st);
 cudaError_t configure_kernels();
+cudaError_t launch_server(const ServerArgs& a, int grid, cudaStream_t st);
 
 }  // namespace hafgb

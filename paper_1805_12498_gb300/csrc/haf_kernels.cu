@@ -117,8 +117,10 @@ struct Ops<cplx> {
   static __device__ __forceinline__ double re(cplx a) { return a.re; }
   static __device__ __forceinline__ double im(cplx a) { return a.im; }
   static __device__ __forceinline__ double absval(cplx a) { return hypot(a.re, a.im); }
+  // Loads of A go through L2 only (ld.global.cg): a job's matrix may sit at
+  // an address an earlier job used, written since by a copy engine.
   static __device__ __forceinline__ cplx load(const double* p, size_t i) {
-    const double2 v = reinterpret_cast<const double2*>(p)[i];
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p) + i);
     return cplx{v.x, v.y};
   }
   static __device__ __forceinline__ cplx from_re(double x) { return cplx{x, 0.0}; }
@@ -166,7 +168,7 @@ struct Ops<double> {
   static __device__ __forceinline__ double re(double a) { return a; }
   static __device__ __forceinline__ double im(double) { return 0.0; }
   static __device__ __forceinline__ double absval(double a) { return fabs(a); }
-  static __device__ __forceinline__ double load(const double* p, size_t i) { return p[i]; }
+  static __device__ __forceinline__ double load(const double* p, size_t i) { return __ldcg(p + i); }
   static __device__ __forceinline__ double from_re(double x) { return x; }
 
   static __device__ __forceinline__ void reflector(double x0, double s0, double nrm2, double& c,
@@ -708,10 +710,10 @@ __device__ void loop_moments_tail(int N, int h, const T* __restrict__ DN, T* U, 
 // One chunk: ceil(count / S) rounds of S subsets (one per group).
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ void process_chunk(const KernelArgs& args, const Chunk& ch, int chunk_id,
-                              unsigned char* wbase, int lane) {
+__device__ void process_chunk(const Job& job, const Chunk& ch, double* __restrict__ partial_out,
+                              const double* __restrict__ tables, const uint64_t* __restrict__ masks,
+                              double* __restrict__ terms_out, unsigned char* wbase, int lane) {
   using O = Ops<T>;
-  const Job job = args.jobs[ch.job];
   const int n = job.n, h = n >> 1, m = ch.m, N = 2 * m, G = ch.G, S = 32 / G, ld = ch.ld;
   const int s = lane / G, g = lane - s * G;
   const bool loops = job.loops != 0;
@@ -730,7 +732,7 @@ __device__ void process_chunk(const KernelArgs& args, const Chunk& ch, int chunk
   T* AC2 = ES + (h + 1);
   int* pos = reinterpret_cast<int*>(AC2 + (h + 1));
   const bool neg = ((h - m) & 1) != 0;
-  const bool term_mode = args.terms_out != nullptr;
+  const bool term_mode = terms_out != nullptr;
 
   double re_hi = 0.0, re_lo = 0.0, im_hi = 0.0, im_lo = 0.0, asum = 0.0;
   uint64_t mask = ch.mask0;
@@ -742,7 +744,7 @@ __device__ void process_chunk(const KernelArgs& args, const Chunk& ch, int chunk
     const bool valid = local < ch.count;
     uint64_t zmask;
     if (term_mode) {
-      zmask = valid ? args.masks[ch.rank0 + local] : ((1ull << m) - 1);
+      zmask = valid ? masks[ch.rank0 + local] : ((1ull << m) - 1);
     } else {
       zmask = valid ? mask : ((1ull << m) - 1);
       for (int q = 0; q < S; ++q) mask = next_comb(mask);  // this group's next subset
@@ -773,11 +775,11 @@ __device__ void process_chunk(const KernelArgs& args, const Chunk& ch, int chunk
     if (loops) loop_moments<T>(tile, ld, N, h, VA, VB, W, TV, U, g, G);
     labudde<T>(tile, ld, N, h, DN, g, G);
     if (loops && N < h) loop_moments_tail<T>(N, h, DN, U, g, G);
-    const T f = series<T>(N, h, DN, U, GS, AC, ES, AC2, loops, args.tables, g, G);
+    const T f = series<T>(N, h, DN, U, GS, AC, ES, AC2, loops, tables, g, G);
     if (term_mode) {
       if (valid && g == 0) {
-        args.terms_out[2 * (ch.rank0 + local)] = O::re(f);
-        args.terms_out[2 * (ch.rank0 + local) + 1] = O::im(f);
+        terms_out[2 * (ch.rank0 + local)] = O::re(f);
+        terms_out[2 * (ch.rank0 + local) + 1] = O::im(f);
       }
     } else if (valid) {
       const double fr = neg ? -O::re(f) : O::re(f);
@@ -802,7 +804,7 @@ __device__ void process_chunk(const KernelArgs& args, const Chunk& ch, int chunk
     t_abs += e;
   }
   if (lane == 0) {
-    double* o = args.partials + 5 * (size_t)chunk_id;
+    double* o = partial_out;
     o[0] = t_re_hi;
     o[1] = t_re_lo;
     o[2] = t_im_hi;
@@ -823,7 +825,133 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) subset_kernel(KernelAr
     if (ci >= args.nchunks) break;
     const int id = args.order[ci];
     const Chunk ch = args.chunks[id];
-    process_chunk<T>(args, ch, id, wbase, lane);
+    const Job job = args.jobs[ch.job];
+    process_chunk<T>(job, ch, args.partials ? args.partials + 5 * (size_t)id : nullptr, args.tables,
+                     args.masks, args.terms_out, wbase, lane);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Server loop.  Warps claim chunk descriptors from a ring in host memory that
+// the host scheduler appends to while the kernel runs (it publishes a count
+// with a release store; a warp reads it with an acquire load and claims the
+// next entry with a compare-and-swap on a device counter).  After its chunk
+// a warp bumps the job's completed-chunk counter; the warp that completes a
+// job adds the job's chunk partials in chunk order and posts the result and
+// a flag to host memory.  A warp with no work sleeps briefly between polls
+// and leaves after idle_ns without work or when asked to stop; the host
+// relaunches the kernel when new work arrives after all warps have left.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned int ld_relaxed_sys(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ long long globaltimer() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <class T>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) server_kernel(ServerArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* wbase = smem + warp * a.warp_bytes;
+  long long idle_since = globaltimer();
+  for (;;) {
+    unsigned long long idx = 0;
+    int status = 0;  // 1: claimed an entry, 2: leave
+    if (lane == 0) {
+      for (;;) {
+        const unsigned long long t = ld_acquire_sys(a.tail);
+        const unsigned long long h = atomicAdd(a.head, 0ull);
+        if (h < t) {
+          if (atomicCAS(a.head, h, h + 1) == h) {
+            idx = h;
+            status = 1;
+            break;
+          }
+          continue;  // another warp took entry h; try the next one
+        }
+        if (ld_relaxed_sys(a.stop) != 0u || globaltimer() - idle_since > a.idle_ns) {
+          status = 2;
+          break;
+        }
+        __nanosleep(2000);
+      }
+    }
+    status = __shfl_sync(kFull, status, 0);
+    if (status == 2) break;
+    idx = __shfl_sync(kFull, idx, 0);
+    __syncwarp();
+    if (lane == 0) *reinterpret_cast<volatile unsigned long long*>(a.head_mirror) = idx + 1;
+    // lane 0 reads the descriptor (host memory, after its acquire) and the
+    // job entry (device memory, through L2) and hands them to the warp
+    Chunk ch;
+    SrvJob sj;
+    {
+      unsigned long long cw[sizeof(Chunk) / 8], jw[sizeof(SrvJob) / 8];
+      if (lane == 0) {
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(a.ring + idx % a.cap);
+#pragma unroll
+        for (int k = 0; k < (int)(sizeof(Chunk) / 8); ++k)
+          asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(cw[k]) : "l"(src + k) : "memory");
+        const Chunk* cp = reinterpret_cast<const Chunk*>(cw);
+        const unsigned long long* js = reinterpret_cast<const unsigned long long*>(a.jobs + cp->job);
+#pragma unroll
+        for (int k = 0; k < (int)(sizeof(SrvJob) / 8); ++k) jw[k] = __ldcg(js + k);
+      }
+#pragma unroll
+      for (int k = 0; k < (int)(sizeof(Chunk) / 8); ++k) cw[k] = __shfl_sync(kFull, cw[k], 0);
+#pragma unroll
+      for (int k = 0; k < (int)(sizeof(SrvJob) / 8); ++k) jw[k] = __shfl_sync(kFull, jw[k], 0);
+      memcpy(&ch, cw, sizeof(Chunk));
+      memcpy(&sj, jw, sizeof(SrvJob));
+    }
+    process_chunk<T>(sj.job, ch, sj.partials + 5 * (size_t)ch.aux, a.tables, nullptr, nullptr, wbase, lane);
+    __threadfence();
+    unsigned int prev = 0;
+    if (lane == 0) prev = atomicAdd(sj.done, 1u);
+    prev = __shfl_sync(kFull, prev, 0);
+    if (prev + 1 == sj.nchunks) {
+      __threadfence();
+      // fixed-order sum of the job's partials: lane l takes chunks l, l+32, ...
+      double rh = 0, rl = 0, ih = 0, il = 0, ab = 0;
+      for (unsigned int c = lane; c < sj.nchunks; c += 32) {
+        const double* p = sj.partials + 5 * (size_t)c;
+        dd_add_dd(rh, rl, __ldcg(p), __ldcg(p + 1));
+        dd_add_dd(ih, il, __ldcg(p + 2), __ldcg(p + 3));
+        ab += __ldcg(p + 4);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double a0 = __shfl_xor_sync(kFull, rh, o), a1 = __shfl_xor_sync(kFull, rl, o);
+        const double b0 = __shfl_xor_sync(kFull, ih, o), b1 = __shfl_xor_sync(kFull, il, o);
+        const double c0 = __shfl_xor_sync(kFull, ab, o);
+        dd_add_dd(rh, rl, a0, a1);
+        dd_add_dd(ih, il, b0, b1);
+        ab += c0;
+      }
+      if (lane == 0) {
+        volatile double* r = sj.result;
+        r[0] = rh;
+        r[1] = ih;
+        r[2] = rl;
+        r[3] = il;
+        r[4] = ab;
+        __threadfence_system();
+        st_release_sys(sj.flag, sj.gen);
+      }
+    }
+    idle_since = globaltimer();
   }
 }
 
@@ -945,6 +1073,9 @@ cudaError_t configure_kernels() {
   cudaError_t e = cudaFuncSetAttribute(subset_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kWarpBytes * kWarpsPerBlock);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(server_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kWarpBytes * kWarpsPerBlock);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(subset_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               kWarpBytes * kWarpsPerBlock);
 }
@@ -976,6 +1107,11 @@ cudaError_t launch_subsets(const KernelArgs& a, int is_real, int grid, cudaStrea
     subset_kernel<double><<<grid, 32 * kWarpsPerBlock, smem, st>>>(a);
   else
     subset_kernel<cplx><<<grid, 32 * kWarpsPerBlock, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_server(const ServerArgs& a, int grid, cudaStream_t st) {
+  server_kernel<cplx><<<grid, 32 * kWarpsPerBlock, a.warp_bytes * kWarpsPerBlock, st>>>(a);
   return cudaGetLastError();
 }
 
