@@ -147,6 +147,74 @@ def batched_leg(count: int, seed: int, reps: int = 3):
             "max_abs_diff_over_abs_sum_vs_single": worst, "timing": "host clock, synchronous calls"}
 
 
+def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
+    """Serving (config 4 shape, scaled): haf/lhaf requests (50/50) on GBS
+    submatrices, n even in [8, n_max] with P(n) proportional to 2^(-n/8),
+    through the continuous-batching server.  The capacity is measured first
+    with all requests submitted at once; the open-loop run then offers
+    Poisson arrivals at `load` x capacity and reports throughput and the
+    p50/p99 of the submit-to-result latency the server records."""
+    import threading as th
+
+    import paper_1805_12498_gb300 as hg
+    from paper_1805_12498_gb300 import inputs
+
+    B = inputs.gbs_kernel(32, 0.88, seed)
+    g = inputs.rng(seed + 3)
+    ns = np.arange(8, n_max + 1, 2)
+    w = 2.0 ** (-ns / 8.0)
+    reqs = []
+    for _ in range(requests):
+        n = int(g.choice(ns, p=w / w.sum()))
+        reqs.append((inputs.repeat_submatrix(B, inputs.click_pattern(n, 32, g)), bool(g.integers(0, 2))))
+    with hg.Server() as srv:
+        for M, loops in reqs[:16]:  # warm the resident kernel and the plans
+            srv.poll(srv.submit(M, loops), timeout_s=120)
+        t = time.perf_counter()
+        tickets = [srv.submit(M, loops) for M, loops in reqs]
+        for tk in tickets:
+            srv.poll(tk, timeout_s=120)
+        capacity = requests / (time.perf_counter() - t)
+        rate = load * capacity
+        gaps = g.exponential(1.0 / rate, size=requests)
+        submitted = []
+        lock = th.Lock()
+
+        def submitter():
+            t_next = time.perf_counter()
+            for (M, loops), gap in zip(reqs, gaps):
+                t_next += gap
+                d = t_next - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tk = srv.submit(M, loops)
+                with lock:
+                    submitted.append(tk)
+
+        thr = th.Thread(target=submitter)
+        t0 = time.perf_counter()
+        thr.start()
+        lat = []
+        k = 0
+        while k < requests:
+            with lock:
+                ready = k < len(submitted)
+                tk = submitted[k] if ready else None
+            if not ready:
+                time.sleep(0.0005)
+                continue
+            lat.append(srv.poll(tk, timeout_s=120).seconds)
+            k += 1
+        thr.join()
+        wall = time.perf_counter() - t0
+    lat = np.array(lat) * 1e3
+    return {"workload": f"{requests} requests, haf/lhaf 50/50, GBS submatrices of a 32-mode kernel (r=0.88), "
+                        f"n even in [8,{n_max}], P(n) ~ 2^(-n/8), Poisson arrivals at {load:g} x capacity",
+            "capacity_req_per_s": capacity, "offered_req_per_s": rate, "throughput_req_per_s": requests / wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max())}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -178,6 +246,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gbs-batch", type=int, default=4096,
                     help="GBS-shaped batch size for the batched leg (0 skips it)")
+    ap.add_argument("--serve-requests", type=int, default=1200,
+                    help="requests in the serving leg (0 skips it)")
+    ap.add_argument("--serve-nmax", type=int, default=40)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -279,6 +350,8 @@ def main():
         }
         if args.gbs_batch > 0:
             line["batched"] = batched_leg(args.gbs_batch, args.seed)
+        if args.serve_requests > 0:
+            line["serving"] = serving_leg(args.serve_requests, args.serve_nmax, args.seed)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(n, args.seed)
         print(json.dumps(line), flush=True)

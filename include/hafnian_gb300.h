@@ -196,15 +196,18 @@ int haf_terms_c128(const double* A, int64_t n, int loops, const uint64_t* masks,
  *                  = 2 doubles; info->seconds = latency from submit to the
  *                  result.  A ticket is collected once (then HAF_ENOTFOUND).
  *   destroy      : lets in-flight work finish, then frees everything.
- * The resident kernel's warps leave after idle_us without work and the
- * scheduler relaunches it when work arrives; no device wait is unbounded.
+ * The resident kernel exits once no warp has claimed a chunk for idle_us,
+ * and the scheduler relaunches it when work arrives; no device wait is
+ * unbounded.  create fails with HAF_EINVAL for max_jobs > 65535 or
+ * ring_entries < 65536.
  * ---------------------------------------------------------------------- */
 typedef struct haf_server haf_server;
 typedef struct haf_server_cfg {
   int64_t max_jobs;     /* jobs admitted at once (default 256, max 65535)      */
   int64_t max_bytes;    /* device memory for admitted jobs (default 256 MiB)   */
-  int64_t ring_entries; /* chunk descriptors in the host ring (default 2^20)   */
+  int64_t ring_entries; /* chunk descriptor ring entries (default 2^20, >= 2^16) */
   int64_t idle_us;      /* resident kernel idles out after this (default 20 ms) */
+  int64_t chunk_us;     /* target warp time per work chunk (default 4 ms)      */
 } haf_server_cfg;
 
 int haf_server_create(const haf_server_cfg* cfg, haf_server** out);

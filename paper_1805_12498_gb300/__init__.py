@@ -155,9 +155,10 @@ class Server:
     haf_server_*): submit haf/lhaf requests of mixed n while others run,
     collect each result once with ``poll``."""
 
-    def __init__(self, max_jobs: int = 0, max_bytes: int = 0, ring_entries: int = 0, idle_us: int = 0):
+    def __init__(self, max_jobs: int = 0, max_bytes: int = 0, ring_entries: int = 0, idle_us: int = 0,
+                 chunk_us: int = 0):
         self._L = _native.lib()
-        cfg = _native.ServerCfg(max_jobs, max_bytes, ring_entries, idle_us)
+        cfg = _native.ServerCfg(max_jobs, max_bytes, ring_entries, idle_us, chunk_us)
         h = ctypes.c_void_p()
         _native.check(self._L.haf_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

@@ -34,7 +34,7 @@ class HafInfo(ctypes.Structure):
 
 class ServerCfg(ctypes.Structure):
     _fields_ = [("max_jobs", ctypes.c_int64), ("max_bytes", ctypes.c_int64),
-                ("ring_entries", ctypes.c_int64), ("idle_us", ctypes.c_int64)]
+                ("ring_entries", ctypes.c_int64), ("idle_us", ctypes.c_int64), ("chunk_us", ctypes.c_int64)]
 
 
 class HafError(RuntimeError):

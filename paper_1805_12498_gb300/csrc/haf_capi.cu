@@ -125,7 +125,14 @@ int build_plan(const std::vector<JobSpec>& jobs, int num_warps, Plan* plan) {
       part_range(binom(h, m), js.part, js.nparts, &rlo, &rhi);
       const uint64_t cnt = rhi - rlo;
       const double per = std::pow((double)N, 3);
-      uint64_t csz = (uint64_t)std::ceil(target / per / S) * S;
+      // a cap on chunk work, but never more than 65,536 chunks per job
+      double tj = target;
+      if (js.max_chunk_units > 0) {
+        double job_total = 0.0;
+        for (int mm = 1; mm <= h; ++mm) job_total += (double)binom(h, mm) * std::pow(2.0 * mm, 3);
+        tj = std::max(std::min(target, js.max_chunk_units), job_total / (double)js.nparts / 65536.0);
+      }
+      uint64_t csz = (uint64_t)std::ceil(tj / per / S) * S;
       csz = std::max<uint64_t>(csz, (uint64_t)S);
       csz = std::min<uint64_t>(csz, (uint64_t)1 << 30);
       for (uint64_t r0 = 0; r0 < cnt; r0 += csz) {

@@ -29,7 +29,8 @@ struct Chunk {
   uint8_t m;       // |Z|; the tile is N = 2m square
   uint8_t G;       // lanes per subset (1,2,4,8,16,32); 32/G subsets per warp
   uint8_t ld;      // tile leading dimension (N or N+1)
-  uint8_t pad[3];
+  uint8_t pad;
+  uint16_t tag;    // server: low 16 bits of the job's generation
   uint32_t aux;    // server: index of the chunk within its job
 };
 static_assert(sizeof(Chunk) == 32, "Chunk layout");
@@ -67,15 +68,18 @@ struct SrvJob {
 static_assert(sizeof(SrvJob) % 8 == 0, "SrvJob is moved as 64-bit words");
 
 struct ServerArgs {
-  const Chunk* ring;                  // device view of the mapped host ring
+  const Chunk* ring;                  // device: chunk descriptors (written by the host's copies)
   unsigned long long cap;             // ring entries
-  const unsigned long long* tail;     // mapped host: chunks published so far
-  unsigned long long* head;           // device: chunks claimed so far
-  unsigned long long* head_mirror;    // mapped host: a recent value of *head
-  const unsigned int* stop;           // mapped host: nonzero asks the warps to leave
+  const unsigned long long* tail;     // device: chunks published so far (host copy, after the entries)
+  unsigned long long* head;           // device: [0] chunks claimed, [1] time of the latest claim,
+                                      // [2..] diagnostic counters
+  unsigned int* stop;                 // device: nonzero makes every warp leave (set by the host's
+                                      // copy at shutdown, or by the first warp that finds the
+                                      // kernel idle)
+  unsigned long long* stats;          // mapped host, diagnostic words (see the server's log)
   const SrvJob* jobs;                 // device job table
   const double* tables;
-  long long idle_ns;                  // a warp leaves after this long without work
+  long long idle_ns;                  // the kernel leaves after this long without a claim
   int warp_bytes;
 };
 constexpr int kMaxSmemPerBlock = 232448;  // 227 KiB opt-in on sm_100/sm_103
@@ -97,6 +101,7 @@ struct JobSpec {
   int is_real;
   int64_t part = 0;  // this job covers part `part` of `nparts` of every size class
   int64_t nparts = 1;
+  double max_chunk_units = 0;  // cap on a chunk's work in N^3 units (0: none)
 };
 struct Plan {
   std::vector<Chunk> chunks;

@@ -487,11 +487,11 @@ __device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__
     T w0, alpha;
     O::reflector(x0, s0, s0 + sig, c, w0, alpha);
     for (int i = i2; i < N; i += G) W[i] = O::scale(tile[i * ld + k], c);
-    if (g == 0) {
-      W[k1] = w0;
-      tile[k1 * ld + k] = alpha;
-    }
+    if (g == 0) W[k1] = w0;
     __syncwarp();
+    // every lane has read x0 by now, so its entry may take alpha (column k
+    // is outside the columns the rest of this step reads)
+    if (g == 0) tile[k1 * ld + k] = alpha;
     range_matvec<T>(tile, ld, k1, N, 0, N, g, G, W, P, X);  // p = A[:, K] w
     __syncwarp();
     T gam = O::zero();
@@ -832,28 +832,34 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) subset_kernel(KernelAr
 }
 
 // ---------------------------------------------------------------------------
-// Server loop.  Warps claim chunk descriptors from a ring in host memory that
-// the host scheduler appends to while the kernel runs (it publishes a count
-// with a release store; a warp reads it with an acquire load and claims the
-// next entry with a compare-and-swap on a device counter).  After its chunk
-// a warp bumps the job's completed-chunk counter; the warp that completes a
-// job adds the job's chunk partials in chunk order and posts the result and
-// a flag to host memory.  A warp with no work sleeps briefly between polls
-// and leaves after idle_ns without work or when asked to stop; the host
-// relaunches the kernel when new work arrives after all warps have left.
+// Server loop.  Warps claim chunk descriptors from a ring in device memory
+// that the host scheduler appends to, by copy-engine transfers, while the
+// kernel runs: the host copies the new descriptors and then the new
+// published count; a warp reads the count (ld.acquire at gpu scope) and
+// claims the next entry with a compare-and-swap on a device counter.  After
+// its chunk a warp bumps the job's completed-chunk counter; the warp that
+// completes a job adds the job's chunk partials in chunk order and posts the
+// result and a flag to host memory (release store at system scope).  A warp
+// with no work sleeps between polls with exponential back-off; when no warp
+// has claimed anything for idle_ns the first warp to notice raises the stop
+// flag and every warp leaves, and the host relaunches the kernel when new
+// work arrives.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
   unsigned long long v;
-  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ unsigned int ld_relaxed_sys(const unsigned int* p) {
+__device__ __forceinline__ unsigned int ld_relaxed_gpu(const unsigned int* p) {
   unsigned int v;
-  asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ void st_release_sys(unsigned int* p, unsigned int v) {
   asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_sys(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ long long globaltimer() {
   long long t;
@@ -866,36 +872,53 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) server_kernel(ServerAr
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* wbase = smem + warp * a.warp_bytes;
-  long long idle_since = globaltimer();
+  unsigned long long* const claims = a.head;                                   // [0]
+  volatile long long* const last_claim = reinterpret_cast<volatile long long*>(a.head + 1);
+  const long long started = globaltimer();
+  unsigned long long t_seen = 0;  // published count this warp has acquired
   for (;;) {
     unsigned long long idx = 0;
     int status = 0;  // 1: claimed an entry, 2: leave
     if (lane == 0) {
+      unsigned long long h = atomicAdd(claims, 0ull);
+      unsigned int nap = 256;
       for (;;) {
-        const unsigned long long t = ld_acquire_sys(a.tail);
-        const unsigned long long h = atomicAdd(a.head, 0ull);
-        if (h < t) {
-          if (atomicCAS(a.head, h, h + 1) == h) {
+        if (h < t_seen) {
+          // entries below t_seen are published; take entry h unless another
+          // warp got there first (then retry with the value it left)
+          const unsigned long long prev = atomicCAS(claims, h, h + 1);
+          if (prev == h) {
             idx = h;
             status = 1;
+            *last_claim = globaltimer();
             break;
           }
-          continue;  // another warp took entry h; try the next one
+          h = prev;
+          continue;
         }
-        if (ld_relaxed_sys(a.stop) != 0u || globaltimer() - idle_since > a.idle_ns) {
+        t_seen = ld_acquire_gpu(a.tail);
+        if (h < t_seen) continue;
+        atomicAdd(a.head + 2, 1ull);  // diagnostic: idle polls
+        if (ld_relaxed_gpu(a.stop) != 0u) {
           status = 2;
           break;
         }
-        __nanosleep(2000);
+        const long long now = globaltimer();
+        if (now - max(started, *last_claim) > a.idle_ns) {
+          atomicExch(a.stop, 1u);
+          status = 2;
+          break;
+        }
+        __nanosleep(nap);
+        nap = min(nap * 2u, 32768u);
+        h = atomicAdd(claims, 0ull);
       }
     }
     status = __shfl_sync(kFull, status, 0);
     if (status == 2) break;
     idx = __shfl_sync(kFull, idx, 0);
-    __syncwarp();
-    if (lane == 0) *reinterpret_cast<volatile unsigned long long*>(a.head_mirror) = idx + 1;
-    // lane 0 reads the descriptor (host memory, after its acquire) and the
-    // job entry (device memory, through L2) and hands them to the warp
+    // lane 0 reads the descriptor and the job entry (device memory, through
+    // L2) and hands them to the warp
     Chunk ch;
     SrvJob sj;
     {
@@ -903,8 +926,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) server_kernel(ServerAr
       if (lane == 0) {
         const unsigned long long* src = reinterpret_cast<const unsigned long long*>(a.ring + idx % a.cap);
 #pragma unroll
-        for (int k = 0; k < (int)(sizeof(Chunk) / 8); ++k)
-          asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(cw[k]) : "l"(src + k) : "memory");
+        for (int k = 0; k < (int)(sizeof(Chunk) / 8); ++k) cw[k] = __ldcg(src + k);
         const Chunk* cp = reinterpret_cast<const Chunk*>(cw);
         const unsigned long long* js = reinterpret_cast<const unsigned long long*>(a.jobs + cp->job);
 #pragma unroll
@@ -917,17 +939,37 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) server_kernel(ServerAr
       memcpy(&ch, cw, sizeof(Chunk));
       memcpy(&sj, jw, sizeof(SrvJob));
     }
+    if (ch.tag != (uint16_t)(sj.gen & 0xffffu)) {
+      // a descriptor that does not belong to the job now in its slot: count
+      // it and leave the job's counters alone (diagnostic; never expected)
+      if (lane == 0) st_relaxed_sys(a.stats + 3, atomicAdd(a.head + 5, 1ull) + 1);
+      continue;
+    }
+    const long long tc0 = globaltimer();
     process_chunk<T>(sj.job, ch, sj.partials + 5 * (size_t)ch.aux, a.tables, nullptr, nullptr, wbase, lane);
     __threadfence();
     unsigned int prev = 0;
-    if (lane == 0) prev = atomicAdd(sj.done, 1u);
+    if (lane == 0) {
+      prev = atomicAdd(sj.done, 1u);
+      // diagnostics: chunks done, total chunk time
+      const unsigned long long c = atomicAdd(a.head + 3, 1ull) + 1;
+      const unsigned long long tt = atomicAdd(a.head + 4, (unsigned long long)(globaltimer() - tc0));
+      if ((c & 255ull) == 0) {
+        st_relaxed_sys(a.stats, c);
+        st_relaxed_sys(a.stats + 1, tt);
+        st_relaxed_sys(a.stats + 2, *reinterpret_cast<volatile unsigned long long*>(a.head + 2));
+      }
+    }
     prev = __shfl_sync(kFull, prev, 0);
+    if (prev >= sj.nchunks && lane == 0) st_relaxed_sys(a.stats + 4, atomicAdd(a.head + 6, 1ull) + 1);
     if (prev + 1 == sj.nchunks) {
       __threadfence();
       // fixed-order sum of the job's partials: lane l takes chunks l, l+32, ...
       double rh = 0, rl = 0, ih = 0, il = 0, ab = 0;
+      unsigned int unwritten = 0;
       for (unsigned int c = lane; c < sj.nchunks; c += 32) {
         const double* p = sj.partials + 5 * (size_t)c;
+        if (__ldcg(p) != __ldcg(p)) ++unwritten;  // diagnostic fill seen: chunk c never wrote
         dd_add_dd(rh, rl, __ldcg(p), __ldcg(p + 1));
         dd_add_dd(ih, il, __ldcg(p + 2), __ldcg(p + 3));
         ab += __ldcg(p + 4);
@@ -940,6 +982,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) server_kernel(ServerAr
         dd_add_dd(ih, il, b0, b1);
         ab += c0;
       }
+      for (int o = 16; o > 0; o >>= 1) unwritten += __shfl_xor_sync(kFull, unwritten, o);
+      if (lane == 0 && unwritten) st_relaxed_sys(a.stats + 5, atomicAdd(a.head + 9, (unsigned long long)unwritten) + unwritten);
       if (lane == 0) {
         volatile double* r = sj.result;
         r[0] = rh;
@@ -951,7 +995,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) server_kernel(ServerAr
         st_release_sys(sj.flag, sj.gen);
       }
     }
-    idle_since = globaltimer();
   }
 }
 

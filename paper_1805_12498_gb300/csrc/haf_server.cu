@@ -6,7 +6,10 @@
 // admitted matrix on the host (pair swap X A, upper-triangle symmetrisation,
 // diagonal, Sec. 3.3 eq. matA), copies it into the job's region of a device
 // arena on a copy stream, and then publishes the job's subset chunks into a
-// ring in host memory that the resident kernel's warps drain.  Chunks of
+// descriptor ring in device memory that the resident kernel's warps drain
+// (the host stages new descriptors in pinned memory and copies them, then
+// the new published count, on one stream, so a warp that sees the count
+// sees the descriptors below it).  Chunks of
 // all admitted jobs are published round robin with a bounded queue depth,
 // so a large-n job is split into chunks that interleave with small jobs
 // that arrive while it runs.  The warp that finishes a job's last chunk
@@ -20,6 +23,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -120,19 +125,31 @@ struct haf_server {
   Arena alloc;
   SrvJob* jobs_dev = nullptr;
   SrvJob* jobs_stage = nullptr;  // pinned
-  unsigned long long* head_dev = nullptr;
+  unsigned int* zeros = nullptr;  // pinned, 256 zero bytes
+  double* nan_src = nullptr;      // pinned NaNs (diagnostic fill of partial slots)
+  size_t nan_len = 0;
+  unsigned long long* head_dev = nullptr;  // [0] claimed, [1] last claim time, [2..] diagnostics
+  unsigned int* stop_dev = nullptr;
   double* tables = nullptr;
-  // mapped host memory
-  Chunk* ring_h = nullptr;
-  Chunk* ring_d = nullptr;
+  // publication: descriptors and the published count reach the device by copies
+  Chunk* ring_dev = nullptr;
+  Chunk* ring_stage = nullptr;  // pinned, same indexing as ring_dev
   unsigned long long cap = 0;
-  unsigned long long* tail_h = nullptr;
-  unsigned long long* mirror_h = nullptr;
-  unsigned int* stop_h = nullptr;
+  unsigned long long* tail_dev = nullptr;
+  unsigned long long* tail_src = nullptr;  // pinned rotating sources of the count copies
+  unsigned int tail_k = 0;
+  unsigned int* flag_src = nullptr;        // pinned: {0, 1} for the stop-flag copies
+  unsigned long long* claimed_h = nullptr; // pinned: read-back of head_dev[0]
+  cudaEvent_t claimed_ev = nullptr;
+  bool claimed_pending = false;
+  uint64_t claimed = 0;
+  cudaStream_t pub = nullptr, status = nullptr;
+  // mapped host memory written by the kernel
+  unsigned long long* stats_h = nullptr;
+  unsigned long long* stats_d = nullptr;
   double* results_h = nullptr;
   unsigned int* flags_h = nullptr;
-  unsigned long long *tail_d = nullptr, *mirror_d = nullptr;
-  unsigned int *stop_d = nullptr, *flags_d = nullptr;
+  unsigned int* flags_d = nullptr;
   double* results_d = nullptr;
   // scheduler
   std::thread thr;
@@ -177,6 +194,15 @@ void prep_host(const JobRec& j, char* dst_at, char* dst_diag) {
   }
 }
 
+// Server jobs are cut into chunks of about cfg.chunk_us of one warp's time
+// (a warp retires roughly 75 N^3 units per microsecond at the FP64 rate), so
+// a newly admitted small job waits at most about one chunk for a warp.
+JobSpec server_spec(const haf_server* s, int n, int loops) {
+  JobSpec js{n, loops, 0};
+  js.max_chunk_units = 75.0 * (double)s->cfg.chunk_us;
+  return js;
+}
+
 size_t job_bytes(int n, size_t nchunks) {
   return al256((size_t)n * n * 16) + al256((size_t)n * 16) + al256(nchunks * 5 * sizeof(double)) + 256;
 }
@@ -187,7 +213,7 @@ bool admit_one(haf_server* s) {
   if (s->pending.empty() || s->free_slots.empty()) return false;
   JobRec& j = *s->jobs[s->pending.front()];
   Plan p;
-  if (build_plan({JobSpec{j.n, j.loops, 0}}, s->sms * kWarpsPerBlock, &p) != HAF_OK) {
+  if (build_plan({server_spec(s, j.n, j.loops)}, s->sms * kWarpsPerBlock, &p) != HAF_OK) {
     s->fatal = HAF_EINVAL;
     s->fatal_msg = "server: planning failed";
     return false;
@@ -206,6 +232,7 @@ bool admit_one(haf_server* s) {
   for (size_t q = 0; q < p.order.size(); ++q) {
     Chunk c = p.chunks[p.order[q]];
     c.job = (uint16_t)j.slot;
+    c.tag = (uint16_t)(j.gen & 0xffffu);
     c.aux = (uint32_t)p.order[q];  // partial slot = index in the job's plan
     j.chunks[q] = c;
   }
@@ -225,7 +252,11 @@ bool admit_one(haf_server* s) {
   sj.gen = j.gen;
   cudaError_t e = cudaMemcpyAsync(dbase, st, (size_t)j.n * j.n * 16, cudaMemcpyHostToDevice, s->copy);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dbase + at_b, st + at_b, (size_t)j.n * 16, cudaMemcpyHostToDevice, s->copy);
-  if (e == cudaSuccess) e = cudaMemsetAsync(sj.done, 0, sizeof(unsigned int), s->copy);
+  // a DMA copy, not cudaMemsetAsync: a memset is a kernel and could not
+  // start while the resident kernel holds every SM
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sj.done, s->zeros, sizeof(unsigned int), cudaMemcpyHostToDevice, s->copy);
+  if (e == cudaSuccess && s->nan_src && p.chunks.size() * 5 <= s->nan_len)
+    e = cudaMemcpyAsync(sj.partials, s->nan_src, p.chunks.size() * 5 * sizeof(double), cudaMemcpyHostToDevice, s->copy);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(s->jobs_dev + j.slot, &sj, sizeof(SrvJob), cudaMemcpyHostToDevice, s->copy);
   if (e == cudaSuccess && !j.uploaded) e = cudaEventCreateWithFlags(&j.uploaded, cudaEventDisableTiming);
@@ -241,9 +272,31 @@ bool admit_one(haf_server* s) {
 
 void scheduler(haf_server* s) {
   cudaSetDevice(s->dev);
-  const uint64_t depth_target = (uint64_t)s->sms * kWarpsPerBlock * 2;
+  const uint64_t depth_target = (uint64_t)s->sms * kWarpsPerBlock;
+  const char* env = std::getenv("HAF_SERVER_LOG");
+  const bool log = env && env[0] == '1';
+  double last_log = now_s();
   std::unique_lock<std::mutex> lk(s->mu);
   while (!s->quit) {
+    if (log && now_s() - last_log > 1.0) {
+      // diagnostic: one line per second with the scheduler's state
+      int st[4] = {0, 0, 0, 0};
+      for (auto& kv : s->jobs) st[kv.second->state]++;
+      const bool up = s->kernel_launched && cudaEventQuery(s->kernel_done) == cudaErrorNotReady;
+      std::fprintf(stderr,
+                   "[haf_server] pending=%zu uploading=%d ready=%d done=%d published=%llu claimed>=%llu "
+                   "kernel=%d launches=%lld free_slots=%zu chunks_done=%llu chunk_ns=%llu idle_polls=%llu "
+                   "stale=%llu over=%llu unwritten=%llu\n",
+                   s->pending.size(), st[kUploading], st[kReady], st[kDone], (unsigned long long)s->published,
+                   (unsigned long long)s->claimed, up ? 1 : 0, (long long)s->launches, s->free_slots.size(),
+                   (unsigned long long)__atomic_load_n(s->stats_h, __ATOMIC_RELAXED),
+                   (unsigned long long)__atomic_load_n(s->stats_h + 1, __ATOMIC_RELAXED),
+                   (unsigned long long)__atomic_load_n(s->stats_h + 2, __ATOMIC_RELAXED),
+                   (unsigned long long)__atomic_load_n(s->stats_h + 3, __ATOMIC_RELAXED),
+                   (unsigned long long)__atomic_load_n(s->stats_h + 4, __ATOMIC_RELAXED),
+                   (unsigned long long)__atomic_load_n(s->stats_h + 5, __ATOMIC_RELAXED));
+      last_log = now_s();
+    }
     bool active = false;
     // 1. completions
     for (auto& kv : s->jobs) {
@@ -268,11 +321,25 @@ void scheduler(haf_server* s) {
       JobRec& j = *kv.second;
       if (j.state == kUploading && cudaEventQuery(j.uploaded) == cudaSuccess) j.state = kReady;
     }
-    // 4. publish round robin, bounded depth and ring space
-    uint64_t oldest = UINT64_MAX;
-    for (auto& kv : s->jobs)
-      if (kv.second->state == kReady) oldest = std::min(oldest, kv.second->first_pub);
-    const uint64_t claimed = __atomic_load_n(s->mirror_h, __ATOMIC_RELAXED);
+    // 4. publish round robin, with bounded depth and ring space.  The count
+    //    of claimed chunks comes from a copy of the device counter (a lower
+    //    bound, refreshed every pass).  A ring slot may be rewritten once its
+    //    entry has been claimed and read: a warp reads the entry it claimed
+    //    before it claims another, so at most one claimed-but-unread entry
+    //    per warp exists, which the margin covers.
+    if (s->claimed_pending && cudaEventQuery(s->claimed_ev) == cudaSuccess) {
+      s->claimed = std::max<uint64_t>(s->claimed, *s->claimed_h);
+      s->claimed_pending = false;
+    }
+    if (!s->claimed_pending) {
+      if (cudaMemcpyAsync(s->claimed_h, s->head_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                          s->status) == cudaSuccess &&
+          cudaEventRecord(s->claimed_ev, s->status) == cudaSuccess)
+        s->claimed_pending = true;
+    }
+    const uint64_t claimed = std::min<uint64_t>(s->claimed, s->published);
+    const uint64_t margin = 4ull * (uint64_t)s->sms * kWarpsPerBlock;
+    const uint64_t lim = (claimed > margin ? claimed - margin : 0) + s->cap;
     bool progress = true;
     const uint64_t before = s->published;
     while (progress) {
@@ -280,40 +347,58 @@ void scheduler(haf_server* s) {
       for (auto& kv : s->jobs) {
         JobRec& j = *kv.second;
         if (j.state != kReady || j.next_pub >= j.chunks.size()) continue;
-        if (s->published - std::min(claimed, s->published) >= depth_target) break;
-        const uint64_t lim = (oldest == UINT64_MAX ? s->published : oldest) + s->cap;
-        if (s->published >= lim) break;
+        if (s->published - claimed >= depth_target || s->published >= lim) break;
         const size_t burst = 4;
         for (size_t q = 0; q < burst && j.next_pub < j.chunks.size() && s->published < lim; ++q) {
-          if (j.first_pub == UINT64_MAX) {
-            j.first_pub = s->published;
-            oldest = std::min(oldest, j.first_pub);
-          }
-          s->ring_h[s->published % s->cap] = j.chunks[j.next_pub++];
+          if (j.first_pub == UINT64_MAX) j.first_pub = s->published;
+          s->ring_stage[s->published % s->cap] = j.chunks[j.next_pub++];
           ++s->published;
           progress = true;
         }
       }
     }
-    if (s->published != before) __atomic_store_n(s->tail_h, (unsigned long long)s->published, __ATOMIC_RELEASE);
+    if (s->published != before) {
+      // copy the new entries (one or two contiguous pieces), then the count
+      cudaError_t e = cudaSuccess;
+      uint64_t p0 = before;
+      while (e == cudaSuccess && p0 < s->published) {
+        const uint64_t i0 = p0 % s->cap;
+        const uint64_t len = std::min<uint64_t>(s->published - p0, s->cap - i0);
+        e = cudaMemcpyAsync(s->ring_dev + i0, s->ring_stage + i0, len * sizeof(Chunk), cudaMemcpyHostToDevice,
+                            s->pub);
+        p0 += len;
+      }
+      unsigned long long* src = s->tail_src + (s->tail_k++ & 4095u);
+      *src = s->published;
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->tail_dev, src, sizeof(unsigned long long), cudaMemcpyHostToDevice, s->pub);
+      if (e != cudaSuccess) {
+        s->fatal = HAF_ECUDA;
+        s->fatal_msg = std::string("server publish: ") + cudaGetErrorString(e);
+      }
+    }
     // 5. keep the resident kernel running while any admitted job is unfinished
     for (auto& kv : s->jobs)
       if (kv.second->state == kReady || kv.second->state == kUploading) active = true;
     if (active && s->published > 0) {
       bool running = s->kernel_launched && cudaEventQuery(s->kernel_done) == cudaErrorNotReady;
       if (!running) {
+        // the previous instance has ended (its warps raised the stop flag
+        // together when idle): clear the flag, in stream order, for the new one
         ServerArgs a;
-        a.ring = s->ring_d;
+        a.ring = s->ring_dev;
         a.cap = s->cap;
-        a.tail = s->tail_d;
+        a.tail = s->tail_dev;
         a.head = s->head_dev;
-        a.head_mirror = s->mirror_d;
-        a.stop = s->stop_d;
+        a.stop = s->stop_dev;
+        a.stats = s->stats_d;
         a.jobs = s->jobs_dev;
         a.tables = s->tables;
         a.idle_ns = (long long)s->cfg.idle_us * 1000LL;
         a.warp_bytes = kWarpBytes;
-        cudaError_t e = launch_server(a, s->sms, s->comp);
+        cudaError_t e = cudaMemcpyAsync(s->stop_dev, s->flag_src, sizeof(unsigned int), cudaMemcpyHostToDevice,
+                                        s->comp);
+        if (e == cudaSuccess) e = launch_server(a, s->sms, s->comp);
         if (e == cudaSuccess) e = cudaEventRecord(s->kernel_done, s->comp);
         if (e != cudaSuccess) {
           s->fatal = HAF_ECUDA;
@@ -345,7 +430,9 @@ int haf_server_create(const haf_server_cfg* cfg, haf_server** out) {
   if (s->cfg.max_jobs > 65535) return sfail(HAF_EINVAL, "haf_server_create: max_jobs > 65535");
   if (s->cfg.max_bytes <= 0) s->cfg.max_bytes = (int64_t)256 << 20;
   if (s->cfg.ring_entries <= 0) s->cfg.ring_entries = (int64_t)1 << 20;
+  if (s->cfg.ring_entries < (int64_t)1 << 16) return sfail(HAF_EINVAL, "haf_server_create: ring_entries < 65536");
   if (s->cfg.idle_us <= 0) s->cfg.idle_us = 20000;
+  if (s->cfg.chunk_us <= 0) s->cfg.chunk_us = 4000;
   SRV_CUDA(cudaGetDevice(&s->dev));
   SRV_CUDA(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->dev));
   SRV_CUDA(configure_kernels());
@@ -359,6 +446,13 @@ int haf_server_create(const haf_server_cfg* cfg, haf_server** out) {
   const int mj = (int)s->cfg.max_jobs;
   SRV_CUDA(cudaMalloc(&s->jobs_dev, sizeof(SrvJob) * mj));
   SRV_CUDA(cudaMallocHost(&s->jobs_stage, sizeof(SrvJob) * mj));
+  SRV_CUDA(cudaMallocHost(&s->zeros, 256));
+  if (std::getenv("HAF_SERVER_LOG") && std::getenv("HAF_SERVER_LOG")[0] == '1') {
+    s->nan_len = (size_t)5 * 65536;
+    SRV_CUDA(cudaMallocHost(&s->nan_src, s->nan_len * sizeof(double)));
+    for (size_t k = 0; k < s->nan_len; ++k) s->nan_src[k] = std::nan("");
+  }
+  std::memset(s->zeros, 0, 256);
   SRV_CUDA(cudaMalloc(&s->head_dev, 256));
   SRV_CUDA(cudaMemset(s->head_dev, 0, 256));
   std::vector<double> tab(256, 0.0);
@@ -367,22 +461,30 @@ int haf_server_create(const haf_server_cfg* cfg, haf_server** out) {
   SRV_CUDA(cudaMalloc(&s->tables, 256 * sizeof(double)));
   SRV_CUDA(cudaMemcpy(s->tables, tab.data(), 256 * sizeof(double), cudaMemcpyHostToDevice));
   s->cap = (unsigned long long)s->cfg.ring_entries;
-  SRV_CUDA(cudaHostAlloc(&s->ring_h, sizeof(Chunk) * s->cap, cudaHostAllocMapped));
-  SRV_CUDA(cudaHostAlloc(&s->tail_h, 256, cudaHostAllocMapped));
-  SRV_CUDA(cudaHostAlloc(&s->mirror_h, 256, cudaHostAllocMapped));
-  SRV_CUDA(cudaHostAlloc(&s->stop_h, 256, cudaHostAllocMapped));
+  SRV_CUDA(cudaStreamCreateWithFlags(&s->pub, cudaStreamNonBlocking));
+  SRV_CUDA(cudaStreamCreateWithFlags(&s->status, cudaStreamNonBlocking));
+  SRV_CUDA(cudaEventCreateWithFlags(&s->claimed_ev, cudaEventDisableTiming));
+  SRV_CUDA(cudaMalloc(&s->ring_dev, sizeof(Chunk) * s->cap));
+  SRV_CUDA(cudaMallocHost(&s->ring_stage, sizeof(Chunk) * s->cap));
+  SRV_CUDA(cudaMalloc(&s->tail_dev, 256));
+  SRV_CUDA(cudaMemset(s->tail_dev, 0, 256));
+  SRV_CUDA(cudaMalloc(&s->stop_dev, 256));
+  SRV_CUDA(cudaMemset(s->stop_dev, 0, 256));
+  SRV_CUDA(cudaMallocHost(&s->tail_src, 4096 * sizeof(unsigned long long)));
+  SRV_CUDA(cudaMallocHost(&s->flag_src, 2 * sizeof(unsigned int)));
+  s->flag_src[0] = 0u;
+  s->flag_src[1] = 1u;
+  SRV_CUDA(cudaMallocHost(&s->claimed_h, sizeof(unsigned long long)));
+  *s->claimed_h = 0;
+  SRV_CUDA(cudaHostAlloc(&s->stats_h, 256, cudaHostAllocMapped));
+  std::memset(s->stats_h, 0, 256);
   SRV_CUDA(cudaHostAlloc(&s->results_h, sizeof(double) * 5 * mj, cudaHostAllocMapped));
   SRV_CUDA(cudaHostAlloc(&s->flags_h, sizeof(unsigned int) * mj, cudaHostAllocMapped));
-  *s->tail_h = 0;
-  *s->mirror_h = 0;
-  *s->stop_h = 0;
   std::memset(s->flags_h, 0, sizeof(unsigned int) * mj);
-  SRV_CUDA(cudaHostGetDevicePointer((void**)&s->ring_d, s->ring_h, 0));
-  SRV_CUDA(cudaHostGetDevicePointer((void**)&s->tail_d, s->tail_h, 0));
-  SRV_CUDA(cudaHostGetDevicePointer((void**)&s->mirror_d, s->mirror_h, 0));
-  SRV_CUDA(cudaHostGetDevicePointer((void**)&s->stop_d, s->stop_h, 0));
+  SRV_CUDA(cudaHostGetDevicePointer((void**)&s->stats_d, s->stats_h, 0));
   SRV_CUDA(cudaHostGetDevicePointer((void**)&s->results_d, s->results_h, 0));
   SRV_CUDA(cudaHostGetDevicePointer((void**)&s->flags_d, s->flags_h, 0));
+  SRV_CUDA(cudaDeviceSynchronize());
   for (int k = mj - 1; k >= 0; --k) s->free_slots.push_back(k);
   s->slot_gen.assign(mj, 0u);
   haf_server* raw = s.release();
@@ -412,7 +514,7 @@ int haf_server_submit(haf_server* s, int kind, const double* A, int64_t n, uint6
     if (np != ni) j->A[((size_t)ni * np + ni) * 2] = 1.0;
     // a job larger than the whole arena could never be admitted
     Plan p;
-    if (build_plan({JobSpec{np, kind, 0}}, s->sms * kWarpsPerBlock, &p) != HAF_OK)
+    if (build_plan({server_spec(s, np, kind)}, s->sms * kWarpsPerBlock, &p) != HAF_OK)
       return sfail(HAF_EINVAL, "haf_server_submit: cannot plan this size");
     if (job_bytes(np, p.chunks.size()) > s->alloc.total)
       return sfail(HAF_ENOMEM, "haf_server_submit: job exceeds the server's device memory");
@@ -465,24 +567,35 @@ int haf_server_destroy(haf_server* s) {
     s->wake.notify_all();
   }
   if (s->thr.joinable()) s->thr.join();
-  __atomic_store_n(s->stop_h, 1u, __ATOMIC_RELEASE);
+  cudaMemcpyAsync(s->stop_dev, s->flag_src + 1, sizeof(unsigned int), cudaMemcpyHostToDevice, s->pub);
+  cudaStreamSynchronize(s->pub);
   cudaStreamSynchronize(s->comp);
   cudaStreamSynchronize(s->copy);
+  cudaStreamSynchronize(s->status);
   for (auto& kv : s->jobs)
     if (kv.second->uploaded) cudaEventDestroy(kv.second->uploaded);
   cudaEventDestroy(s->kernel_done);
+  cudaEventDestroy(s->claimed_ev);
   cudaFree(s->arena);
   cudaFreeHost(s->stage);
   cudaFree(s->jobs_dev);
   cudaFreeHost(s->jobs_stage);
+  cudaFreeHost(s->zeros);
+  if (s->nan_src) cudaFreeHost(s->nan_src);
   cudaFree(s->head_dev);
+  cudaFree(s->stop_dev);
   cudaFree(s->tables);
-  cudaFreeHost(s->ring_h);
-  cudaFreeHost(s->tail_h);
-  cudaFreeHost(s->mirror_h);
-  cudaFreeHost(s->stop_h);
+  cudaFree(s->ring_dev);
+  cudaFreeHost(s->ring_stage);
+  cudaFree(s->tail_dev);
+  cudaFreeHost(s->tail_src);
+  cudaFreeHost(s->flag_src);
+  cudaFreeHost(s->claimed_h);
+  cudaFreeHost(s->stats_h);
   cudaFreeHost(s->results_h);
   cudaFreeHost(s->flags_h);
+  cudaStreamDestroy(s->pub);
+  cudaStreamDestroy(s->status);
   cudaStreamDestroy(s->comp);
   cudaStreamDestroy(s->copy);
   delete s;
