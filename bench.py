@@ -147,6 +147,46 @@ def batched_leg(count: int, seed: int, reps: int = 3):
             "max_abs_diff_over_abs_sum_vs_single": worst, "timing": "host clock, synchronous calls"}
 
 
+def precision_leg(seed: int, value48=None):
+    """Precision study (config 3 shape): FP32-bulk mode against FP64 at n = 40
+    and 48 on a complex Gaussian matrix and on a GBS submatrix (haf).  Errors
+    of the values are relative to abs_sum = sum_Z |f(Z)| (the stated form) and
+    to |haf|; sampled summands of the two modes against each other (the
+    tests pin both to the binary128 oracle)."""
+    import paper_1805_12498_gb300 as hg
+    from paper_1805_12498_gb300 import inputs
+
+    rows = []
+    for kind in ("gauss", "gbs"):
+        for n in (40, 48):
+            if kind == "gauss":
+                A = inputs.complex_gaussian_symmetric(n, seed if n == 48 else seed + n)
+            else:
+                B = inputs.gbs_kernel(32, 0.88, seed + n)
+                A = inputs.repeat_submatrix(B, inputs.click_pattern(n, 32, inputs.rng(seed + n + 7)))
+            if kind == "gauss" and n == 48 and value48 is not None:
+                v64, a64, t64 = value48
+            else:
+                t = time.perf_counter()
+                r = hg.haf_info(A)
+                v64, a64, t64 = r.value, r.abs_sum, time.perf_counter() - t
+            hg.haf_info(A, precision="fp32")
+            t = time.perf_counter()
+            r32 = hg.haf_info(A, precision="fp32")
+            t32 = time.perf_counter() - t
+            d = abs(r32.value - v64)
+            masks = inputs.random_masks(n // 2, 1024, seed=seed + n)
+            f64 = hg.haf_terms(A, masks)
+            rel = np.abs(hg.haf_terms(A, masks, precision="fp32") - f64) / np.abs(f64)
+            rows.append({"input": kind, "n": n, "err_over_abs_sum": d / a64,
+                         "err_over_abs_value": d / max(abs(v64), 1e-300), "abs_value_over_abs_sum": abs(v64) / a64,
+                         "s_fp64": t64, "s_fp32": t32, "speedup": t64 / t32,
+                         "term_rel_err_median": float(np.median(rel)), "term_rel_err_max": float(rel.max())})
+    return {"workload": "haf, n = 40 and 48, complex Gaussian (config 0 recipe) and GBS submatrix (config 2 recipe); "
+                        "FP32 bulk (single-precision Householder + La Budde) vs FP64; 1024 sampled summands per case",
+            "stated_tol_over_abs_sum": hg.HAF_FP32_REL_TOL, "rows": rows}
+
+
 def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
     """Serving (config 4 shape, scaled): haf/lhaf requests (50/50) on GBS
     submatrices, n even in [8, n_max] with P(n) proportional to 2^(-n/8),
@@ -249,6 +289,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=1200,
                     help="requests in the serving leg (0 skips it)")
     ap.add_argument("--serve-nmax", type=int, default=40)
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP32-vs-FP64 precision leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -313,6 +354,7 @@ def main():
     info = _native.HafInfo()
     L.haf_c128(ctypes.cast(pinned.data_ptr(), _native._DP), n, host_out.ctypes.data_as(_native._DP),
                ctypes.byref(info))
+    launches_per_step = int(info.launches)  # prep + subset-kernel launches + finalize
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -342,16 +384,22 @@ def main():
             "result": {"re": float(res[0] + res[2]), "im": float(res[1] + res[3]), "abs_sum": float(res[4])},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved / peak_tflops, "traffic": None,
-                         "note": "FP64 pipe; peak = DFMA probe measured in this run (of measured)"},
+                         "note": "FP64 pipe; peak = DFMA probe measured in this run (of measured); achieved = "
+                                 "(44/3) 2^h h^2 (h+3) flops per step / CUDA-event step time; a step is the "
+                                 f"{launches_per_step} launches of one haf_launch (prep, subset-kernel launches, "
+                                 "finalize), the subset kernel >99.9% of it"},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": n * n * 16,
                     "d2h_bytes_per_step": 5 * 8},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks.summary(),
         }
         if args.gbs_batch > 0:
             line["batched"] = batched_leg(args.gbs_batch, args.seed)
         if args.serve_requests > 0:
             line["serving"] = serving_leg(args.serve_requests, args.serve_nmax, args.seed)
+        if not args.no_precision and world == 1:
+            line["precision"] = precision_leg(args.seed, (complex(res[0] + res[2], res[1] + res[3]), float(res[4]),
+                                                          ms_step * 1e-3))
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(n, args.seed)
         print(json.dumps(line), flush=True)

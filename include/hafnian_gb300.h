@@ -64,8 +64,21 @@ extern "C" {
 #define HAF_ESMALL (-7)    /* caller-supplied workspace too small                  */
 
 /* flags */
-#define HAF_FLAG_LOOPS (1u << 0) /* loop hafnian (used by the *_launch forms)   */
+#define HAF_FLAG_LOOPS (1u << 0) /* loop hafnian                                 */
 #define HAF_FLAG_REAL (1u << 1)  /* A is real float64, not complex128           */
+#define HAF_FLAG_FP32 (1u << 2)  /* FP32-bulk precision mode (see below)         */
+
+/* FP32-bulk precision mode.  With HAF_FLAG_FP32 the gather of B, the
+ * Householder reduction, the loop moments and La Budde's recurrence run in
+ * single precision (complex64 / float32) while the power series, f(Z) and
+ * the double-double subset sum stay FP64.  Its error against the FP64
+ * oracle is measured, not bounded a priori; the mode is offered only for
+ * n <= HAF_FP32_MAX_N, the sizes at which the measured error stayed within
+ * HAF_FP32_REL_TOL * abs_sum (abs_sum = sum_Z |f(Z)|).  Calls with larger n
+ * return HAF_EINVAL.  Whether that is accurate enough for a given use
+ * depends on |haf| / abs_sum, which the library reports with each value. */
+#define HAF_FP32_MAX_N 56
+#define HAF_FP32_REL_TOL 1e-4
 
 /* Per-call report. */
 typedef struct haf_info {
@@ -88,6 +101,10 @@ int haf_c128(const double* A, int64_t n, double* out, haf_info* info);
 int lhaf_c128(const double* A, int64_t n, double* out, haf_info* info);
 int haf_f64(const double* A, int64_t n, double* out, haf_info* info);
 int lhaf_f64(const double* A, int64_t n, double* out, haf_info* info);
+/* The same with flags: HAF_FLAG_LOOPS (lhaf), HAF_FLAG_REAL (A float64,
+ * out 1 double), HAF_FLAG_FP32 (precision mode above).  Unknown flags:
+ * HAF_EINVAL. */
+int haf_eval(const double* A, int64_t n, uint32_t flags, double* out, haf_info* info);
 
 /* ------------------------------------------------------------------------
  * Batched: `count` independent matrices of possibly different sizes run in
@@ -100,6 +117,10 @@ int haf_c128_batched(const double* const* As, const int64_t* ns, int64_t count, 
                      haf_info* infos);
 int lhaf_c128_batched(const double* const* As, const int64_t* ns, int64_t count, double* outs,
                       haf_info* infos);
+/* The same with flags: HAF_FLAG_LOOPS, HAF_FLAG_FP32 (complex128 input only;
+ * HAF_FLAG_REAL is rejected). */
+int haf_batched(const double* const* As, const int64_t* ns, int64_t count, uint32_t flags, double* outs,
+                haf_info* infos);
 
 /* ------------------------------------------------------------------------
  * Sharding one matrix over several GPUs or processes (the subset sum splits
@@ -178,6 +199,47 @@ int haf_launch_noalloc(const double* dA, int64_t n, uint32_t flags, double* d_ou
  * ---------------------------------------------------------------------- */
 int haf_terms_c128(const double* A, int64_t n, int loops, const uint64_t* masks, int64_t count,
                    double* terms);
+/* The same with flags (HAF_FLAG_LOOPS, HAF_FLAG_FP32; complex128 input). */
+int haf_terms(const double* A, int64_t n, uint32_t flags, const uint64_t* masks, int64_t count,
+              double* terms);
+
+/* ------------------------------------------------------------------------
+ * Autotuner (no counterpart in the paper).  The launch shape of a plan is
+ * the number of warps per CTA (4, 8 or 16: the shared-memory slice of each
+ * warp, hence the lanes per subset and the subsets per CTA, follow from it)
+ * and the chunk granularity (about chunks_per_warp chunks of subsets per
+ * resident warp).  haf_tune times every feasible shape (3 x 4 candidates,
+ * each one warm-up plus `reps` launches of one hafnian of size n on a
+ * synthetic matrix -- for large n this takes ~13 (reps+1) single-hafnian
+ * times) and records the fastest for (n, flags) on the current device;
+ * later haf_eval/haf_c128/haf_launch/haf_part calls with that key use it.
+ * haf_tune_set records a shape without timing (e.g. one saved earlier).
+ * haf_batched_tune does the same for one batch (its list of sizes and
+ * flags), timing graph replays of the whole batch; later haf_batched /
+ * *_c128_batched calls with the same sizes use the result.
+ *   out->warps_per_block, out->chunks_per_warp : the chosen shape
+ *   out->ms          : its mean time per launch (or per batch)
+ *   out->ms_default  : the default shape's time (-1 if not a candidate)
+ *   out->candidates  : shapes timed
+ * ---------------------------------------------------------------------- */
+typedef struct haf_tune_result {
+  int32_t warps_per_block;
+  int32_t chunks_per_warp;
+  double ms;
+  double ms_default;
+  int32_t candidates;
+} haf_tune_result;
+int haf_tune(int64_t n, uint32_t flags, int32_t reps, haf_tune_result* out);
+/* Host-only view of the plan a shape gives (for tests and tools): out[8] =
+ * {chunks, launches (segments), warps per CTA of segments 0..2, subsets of
+ * segments 0..2}.  Size classes whose tiles do not fit a warp's slice at
+ * the requested warps per CTA form later segments with fewer warps.
+ * `sms` is the SM count the chunk sizes are planned for. */
+int haf_plan_stats(int64_t n, uint32_t flags, int32_t warps_per_block, int32_t chunks_per_warp, int32_t sms,
+                   int64_t* out);
+int haf_tune_set(int64_t n, uint32_t flags, int32_t warps_per_block, int32_t chunks_per_warp);
+int haf_batched_tune(const double* const* As, const int64_t* ns, int64_t count, uint32_t flags, int32_t reps,
+                     haf_tune_result* out);
 
 /* ------------------------------------------------------------------------
  * Server: continuous batching of haf / lhaf requests on one GPU.

@@ -10,6 +10,8 @@ computed by the CUDA library; this module only marshals arguments.
 The hafnian is the sum over perfect matchings of the products of the
 matched entries (Sec. 2); it is evaluated with the O(n^3 2^{n/2}) signed
 subset sum of Sec. 3 on the GPU in FP64 with double-double accumulation.
+``precision="fp32"`` selects the FP32-bulk mode (single-precision
+reduction and La Budde recurrence, FP64 series and sum; n <= HAF_FP32_MAX_N).
 """
 from __future__ import annotations
 
@@ -18,12 +20,23 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import _native
-from ._native import HAF_FLAG_LOOPS, HAF_FLAG_REAL, HAF_MAX_N, HafError  # noqa: F401
+from . import _native, tuning
+from ._native import HAF_FLAG_FP32, HAF_FLAG_LOOPS, HAF_FLAG_REAL, HAF_MAX_N, HafError  # noqa: F401
 
 __all__ = ["haf", "lhaf", "haf_info", "haf_batched", "haf_terms", "workspace_bytes",
-           "haf_launch", "haf_part", "part_subsets", "combine", "Server", "fp64_peak", "HafError",
-           "HAF_MAX_N"]
+           "haf_launch", "haf_part", "part_subsets", "combine", "Server", "fp64_peak", "tune",
+           "tune_set", "batched_tune", "HafError", "HAF_MAX_N", "HAF_FP32_MAX_N", "HAF_FP32_REL_TOL"]
+
+# FP32-bulk mode: offered for n <= HAF_FP32_MAX_N (include/hafnian_gb300.h)
+HAF_FP32_MAX_N = 56
+HAF_FP32_REL_TOL = 1e-4
+
+
+def _flags(loops: bool = False, real: bool = False, precision: str = "fp64") -> int:
+    if precision not in ("fp64", "fp32"):
+        raise ValueError("precision must be 'fp64' or 'fp32'")
+    return ((HAF_FLAG_LOOPS if loops else 0) | (HAF_FLAG_REAL if real else 0)
+            | (HAF_FLAG_FP32 if precision == "fp32" else 0))
 
 
 @dataclass
@@ -43,45 +56,56 @@ def _prep(A, real: bool) -> np.ndarray:
     return np.ascontiguousarray(A, dtype=np.float64 if real else np.complex128)
 
 
-def haf_info(A, loops: bool = False, real: bool | None = None) -> Info:
+def haf_info(A, loops: bool = False, real: bool | None = None, precision: str = "fp64") -> Info:
     """Hafnian (or loop hafnian) of A with the per-call report."""
+    tuning.ensure_loaded()
     if real is None:
         real = not np.iscomplexobj(A)
     A = _prep(A, real)
     L = _native.lib()
-    fn = {(False, False): L.haf_c128, (True, False): L.lhaf_c128,
-          (False, True): L.haf_f64, (True, True): L.lhaf_f64}[(bool(loops), bool(real))]
     out = np.zeros(2)
     info = _native.HafInfo()
-    _native.check(fn(A.ctypes.data_as(_native._DP), A.shape[0], out.ctypes.data_as(_native._DP),
-                     ctypes.byref(info)))
+    if precision == "fp64":
+        fn = {(False, False): L.haf_c128, (True, False): L.lhaf_c128,
+              (False, True): L.haf_f64, (True, True): L.lhaf_f64}[(bool(loops), bool(real))]
+        _native.check(fn(A.ctypes.data_as(_native._DP), A.shape[0], out.ctypes.data_as(_native._DP),
+                         ctypes.byref(info)))
+    else:
+        _native.check(L.haf_eval(A.ctypes.data_as(_native._DP), A.shape[0], _flags(loops, real, precision),
+                                 out.ctypes.data_as(_native._DP), ctypes.byref(info)))
     val = complex(out[0], 0.0 if real else out[1])
     return Info(val, info.abs_sum, complex(info.value_lo[0], info.value_lo[1]), info.subsets,
                 info.seconds, info.launches)
 
 
-def haf(A, loops: bool = False):
+def haf(A, loops: bool = False, precision: str = "fp64"):
     """haf(A) (Sec. 2, eq. hafA).  Real input gives a float, complex a complex."""
-    r = haf_info(A, loops)
+    r = haf_info(A, loops, precision=precision)
     return r.value.real if not np.iscomplexobj(A) else r.value
 
 
-def lhaf(A):
+def lhaf(A, precision: str = "fp64"):
     """Loop hafnian lhaf(A) (Sec. 2)."""
-    return haf(A, loops=True)
+    return haf(A, loops=True, precision=precision)
 
 
-def haf_batched(mats, loops: bool = False, with_info: bool = False):
-    """Hafnians of a list of complex matrices of mixed sizes in one launch."""
+def _batch_args(mats):
     mats = [_prep(M, False) for M in mats]
     count = len(mats)
     ptrs = (_native._DP * max(1, count))(*[M.ctypes.data_as(_native._DP) for M in mats])
     ns = np.array([M.shape[0] for M in mats], dtype=np.int64)
+    return mats, count, ptrs, ns
+
+
+def haf_batched(mats, loops: bool = False, with_info: bool = False, precision: str = "fp64"):
+    """Hafnians of a list of complex matrices of mixed sizes in one launch."""
+    tuning.ensure_loaded()
+    mats, count, ptrs, ns = _batch_args(mats)
     outs = np.zeros(2 * max(1, count))
     infos = (_native.HafInfo * max(1, count))()
     L = _native.lib()
-    fn = L.lhaf_c128_batched if loops else L.haf_c128_batched
-    _native.check(fn(ptrs, ns.ctypes.data_as(_native._I64P), count, outs.ctypes.data_as(_native._DP), infos))
+    _native.check(L.haf_batched(ptrs, ns.ctypes.data_as(_native._I64P), count, _flags(loops, False, precision),
+                                outs.ctypes.data_as(_native._DP), infos))
     vals = outs[0:2 * count:2] + 1j * outs[1:2 * count:2]
     if not with_info:
         return vals
@@ -89,19 +113,20 @@ def haf_batched(mats, loops: bool = False, with_info: bool = False):
                        infos[i].seconds, infos[i].launches) for i in range(count)]
 
 
-def haf_terms(A, masks, loops: bool = False) -> np.ndarray:
+def haf_terms(A, masks, loops: bool = False, precision: str = "fp64") -> np.ndarray:
     """Unsigned summands f(Z) for the given subset bitmasks (Sec. 3.3)."""
     A = _prep(A, False)
     masks = np.ascontiguousarray(np.asarray(masks, dtype=np.uint64))
     out = np.zeros(2 * max(1, masks.size))
-    _native.check(_native.lib().haf_terms_c128(
-        A.ctypes.data_as(_native._DP), A.shape[0], int(bool(loops)),
+    _native.check(_native.lib().haf_terms(
+        A.ctypes.data_as(_native._DP), A.shape[0], _flags(loops, False, precision),
         masks.ctypes.data_as(_native._U64P), masks.size, out.ctypes.data_as(_native._DP)))
     return out[0:2 * masks.size:2] + 1j * out[1:2 * masks.size:2]
 
 
-def workspace_bytes(n: int, loops: bool = False, real: bool = False) -> int:
-    flags = (HAF_FLAG_LOOPS if loops else 0) | (HAF_FLAG_REAL if real else 0)
+def workspace_bytes(n: int, loops: bool = False, real: bool = False, precision: str = "fp64") -> int:
+    tuning.ensure_loaded()
+    flags = _flags(loops, real, precision)
     b = _native.lib().haf_workspace_bytes(n, flags)
     if b == 0:
         raise HafError(_native.HAF_EINVAL, f"no workspace size for n={n}")
@@ -109,23 +134,26 @@ def workspace_bytes(n: int, loops: bool = False, real: bool = False) -> int:
 
 
 def haf_launch(dA_ptr: int, n: int, d_out_ptr: int, d_work_ptr: int, ws_bytes: int,
-               stream_ptr: int = 0, loops: bool = False, real: bool = False) -> None:
+               stream_ptr: int = 0, loops: bool = False, real: bool = False, precision: str = "fp64") -> None:
     """Enqueue a hafnian on device memory (raw pointers, e.g. torch
     ``tensor.data_ptr()`` and ``torch.cuda.current_stream().cuda_stream``).
     The 5-double record {re_hi, im_hi, re_lo, im_lo, abs_sum} lands at
     d_out_ptr when the stream reaches it."""
-    flags = (HAF_FLAG_LOOPS if loops else 0) | (HAF_FLAG_REAL if real else 0)
+    tuning.ensure_loaded()
+    flags = _flags(loops, real, precision)
     _native.check(_native.lib().haf_launch(dA_ptr, n, flags, d_out_ptr, d_work_ptr, ws_bytes, stream_ptr))
 
 
-def haf_part(A, part: int, nparts: int, loops: bool = False, real: bool | None = None) -> np.ndarray:
+def haf_part(A, part: int, nparts: int, loops: bool = False, real: bool | None = None,
+             precision: str = "fp64") -> np.ndarray:
     """Record {re_hi, im_hi, re_lo, im_lo, abs_sum} of part `part` of `nparts`
     of the subset sum (each size class cut into nparts contiguous slices);
     runs on the current CUDA device.  Combine the parts with ``combine``."""
+    tuning.ensure_loaded()
     if real is None:
         real = not np.iscomplexobj(A)
     A = _prep(A, real)
-    flags = (HAF_FLAG_LOOPS if loops else 0) | (HAF_FLAG_REAL if real else 0)
+    flags = _flags(loops, real, precision)
     rec = np.zeros(5)
     info = _native.HafInfo()
     _native.check(_native.lib().haf_part(A.ctypes.data_as(_native._DP), A.shape[0], flags, part, nparts,
@@ -195,6 +223,34 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def tune(n: int, loops: bool = False, real: bool = False, precision: str = "fp64", reps: int = 1) -> dict:
+    """Time every launch shape for a hafnian of size n with these flags and
+    keep the fastest for later calls (haf_tune).  Returns the chosen shape
+    and the times of it and of the default shape."""
+    r = _native.TuneResult()
+    _native.check(_native.lib().haf_tune(n, _flags(loops, real, precision), reps, ctypes.byref(r)))
+    return {"warps_per_block": r.warps_per_block, "chunks_per_warp": r.chunks_per_warp, "ms": r.ms,
+            "ms_default": r.ms_default, "candidates": r.candidates}
+
+
+def tune_set(n: int, warps_per_block: int, chunks_per_warp: int, loops: bool = False, real: bool = False,
+             precision: str = "fp64") -> None:
+    """Record a launch shape for (n, flags) without timing (haf_tune_set)."""
+    _native.check(_native.lib().haf_tune_set(n, _flags(loops, real, precision), warps_per_block,
+                                             chunks_per_warp))
+
+
+def batched_tune(mats, loops: bool = False, precision: str = "fp64", reps: int = 1) -> dict:
+    """Tune the launch shape of one batch (its size list and flags) by timing
+    graph replays of the whole batch (haf_batched_tune)."""
+    mats, count, ptrs, ns = _batch_args(mats)
+    r = _native.TuneResult()
+    _native.check(_native.lib().haf_batched_tune(ptrs, ns.ctypes.data_as(_native._I64P), count,
+                                                 _flags(loops, False, precision), reps, ctypes.byref(r)))
+    return {"warps_per_block": r.warps_per_block, "chunks_per_warp": r.chunks_per_warp, "ms": r.ms,
+            "ms_default": r.ms_default, "candidates": r.candidates}
 
 
 def fp64_peak() -> tuple[float, float]:

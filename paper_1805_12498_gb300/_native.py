@@ -23,6 +23,7 @@ HAF_ENOTFOUND = -6
 HAF_ESMALL = -7
 HAF_FLAG_LOOPS = 1
 HAF_FLAG_REAL = 2
+HAF_FLAG_FP32 = 4
 HAF_MAX_N = 56
 
 
@@ -30,6 +31,11 @@ class HafInfo(ctypes.Structure):
     _fields_ = [("abs_sum", ctypes.c_double), ("value_lo", ctypes.c_double * 2),
                 ("subsets", ctypes.c_int64), ("seconds", ctypes.c_double),
                 ("launches", ctypes.c_int64)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("warps_per_block", ctypes.c_int32), ("chunks_per_warp", ctypes.c_int32),
+                ("ms", ctypes.c_double), ("ms_default", ctypes.c_double), ("candidates", ctypes.c_int32)]
 
 
 class ServerCfg(ctypes.Structure):
@@ -82,6 +88,23 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         L.haf_launch.restype = ctypes.c_int
         L.haf_terms_c128.argtypes = [_DP, ctypes.c_int64, ctypes.c_int, _U64P, ctypes.c_int64, _DP]
         L.haf_terms_c128.restype = ctypes.c_int
+        L.haf_terms.argtypes = [_DP, ctypes.c_int64, ctypes.c_uint32, _U64P, ctypes.c_int64, _DP]
+        L.haf_terms.restype = ctypes.c_int
+        L.haf_eval.argtypes = [_DP, ctypes.c_int64, ctypes.c_uint32, _DP, ctypes.POINTER(HafInfo)]
+        L.haf_eval.restype = ctypes.c_int
+        L.haf_batched.argtypes = [ctypes.POINTER(_DP), _I64P, ctypes.c_int64, ctypes.c_uint32, _DP,
+                                  ctypes.POINTER(HafInfo)]
+        L.haf_batched.restype = ctypes.c_int
+        L.haf_tune.argtypes = [ctypes.c_int64, ctypes.c_uint32, ctypes.c_int32, ctypes.POINTER(TuneResult)]
+        L.haf_tune.restype = ctypes.c_int
+        L.haf_plan_stats.argtypes = [ctypes.c_int64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32, _I64P]
+        L.haf_plan_stats.restype = ctypes.c_int
+        L.haf_tune_set.argtypes = [ctypes.c_int64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32]
+        L.haf_tune_set.restype = ctypes.c_int
+        L.haf_batched_tune.argtypes = [ctypes.POINTER(_DP), _I64P, ctypes.c_int64, ctypes.c_uint32,
+                                       ctypes.c_int32, ctypes.POINTER(TuneResult)]
+        L.haf_batched_tune.restype = ctypes.c_int
         L.haf_part.argtypes = [_DP, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, _DP,
                                ctypes.POINTER(HafInfo)]
         L.haf_part.restype = ctypes.c_int

@@ -76,12 +76,15 @@ struct SizeCfg {
   int ld;
 };
 
-// Smallest lane-group width whose S = 32/G subsets fit the warp slice.
-bool choose_cfg(int N, int h, int elem, SizeCfg* out) {
+// Smallest lane-group width whose S = 32/G subsets fit the warp slice
+// (kernel kind `kind`, `warp_bytes` of shared memory per warp).
+bool choose_cfg(int N, int h, int kind, int warp_bytes, SizeCfg* out) {
+  const int sb = bulk_elem_bytes(kind), ss = series_elem_bytes(kind);
+  const bool mixed = kind_mixed(kind);
   for (int ld : {N + 1, N}) {
     for (int G = 1; G <= 32; G *= 2) {
       const int S = 32 / G;
-      if ((long)S * subset_bytes(N, ld, h, elem) <= kWarpBytes) {
+      if ((long)S * subset_bytes(N, ld, h, sb, ss, mixed) <= warp_bytes) {
         out->G = G;
         out->ld = ld;
         return true;
@@ -100,62 +103,103 @@ void part_range(uint64_t cnt, int64_t p, int64_t P, uint64_t* lo, uint64_t* hi) 
   *hi = (uint64_t)(c * (unsigned __int128)(p + 1) / (unsigned __int128)P);
 }
 
-int build_plan(const std::vector<JobSpec>& jobs, int num_warps, Plan* plan) {
+int build_plan(const std::vector<JobSpec>& jobs, int sms, const PlanCfg& pc, Plan* plan) {
   plan->chunks.clear();
   plan->order.clear();
+  plan->segs.clear();
   plan->job_begin.assign(1, 0);
-  // total work (in N^3 units) to size the chunks
-  double total = 0.0;
-  for (const JobSpec& js : jobs) {
-    const int h = js.n / 2;
-    for (int m = 1; m <= h; ++m) total += (double)binom(h, m) * std::pow(2.0 * m, 3) / (double)js.nparts;
-  }
-  const double target = std::max(1.0, total / (double)(num_warps * 8));
-  std::vector<double> cost;
+  plan->subsets = 0;
+  if (pc.wpb != 4 && pc.wpb != 8 && pc.wpb != 16) return fail(HAF_EINVAL, "warps per CTA must be 4, 8 or 16");
+  if (pc.chunks_per_warp < 1 || pc.chunks_per_warp > 64) return fail(HAF_EINVAL, "chunks per warp out of range");
+  const int kind = jobs.empty() ? kKindC128 : kernel_kind(jobs[0].is_real, jobs[0].prec);
+  for (const JobSpec& js : jobs)
+    if (kernel_kind(js.is_real, js.prec) != kind) return fail(HAF_EINVAL, "jobs of one plan differ in type");
+  plan->kind = kind;
+  // Every size class (job, m) runs with the requested warps per CTA, or
+  // fewer where its tile does not fit one warp's slice of shared memory;
+  // each warps-per-CTA value present becomes one launch (segment).
+  struct Cls {
+    int job, m, wpb;
+    SizeCfg cfg;
+    uint64_t rlo, cnt;
+  };
+  std::vector<Cls> cls;
+  double work[17] = {0};  // N^3 units per warps-per-CTA value
   for (size_t jb = 0; jb < jobs.size(); ++jb) {
     const JobSpec& js = jobs[jb];
     const int h = js.n / 2;
-    const int elem = js.is_real ? 8 : 16;
     for (int m = 1; m <= h; ++m) {
-      const int N = 2 * m;
-      SizeCfg cfg;
-      if (!choose_cfg(N, h, elem, &cfg)) return fail(HAF_EINVAL, "matrix too large for the shared-memory plan");
-      const int S = 32 / cfg.G;
-      uint64_t rlo, rhi;
-      part_range(binom(h, m), js.part, js.nparts, &rlo, &rhi);
-      const uint64_t cnt = rhi - rlo;
+      Cls c;
+      c.job = (int)jb;
+      c.m = m;
+      c.wpb = pc.wpb;
+      while (!choose_cfg(2 * m, h, kind, warp_bytes_for(c.wpb), &c.cfg)) {
+        if (c.wpb == 4) return fail(HAF_EINVAL, "matrix too large for the shared-memory plan");
+        c.wpb /= 2;
+      }
+      uint64_t rhi;
+      part_range(binom(h, m), js.part, js.nparts, &c.rlo, &rhi);
+      c.cnt = rhi - c.rlo;
+      work[c.wpb] += (double)c.cnt * std::pow(2.0 * m, 3);
+      cls.push_back(c);
+    }
+  }
+  // Chunks in (job, m) order, so each job's chunk ids are contiguous (the
+  // finalize sums them in id order); each segment sized for its own work.
+  std::vector<double> cost;
+  std::vector<int> seg_of;
+  size_t ci = 0;
+  for (size_t jb = 0; jb < jobs.size(); ++jb) {
+    const JobSpec& js = jobs[jb];
+    const int h = js.n / 2;
+    double job_total = 0.0;
+    for (int mm = 1; mm <= h; ++mm) job_total += (double)binom(h, mm) * std::pow(2.0 * mm, 3);
+    for (; ci < cls.size() && cls[ci].job == (int)jb; ++ci) {
+      const Cls& c = cls[ci];
+      const int N = 2 * c.m, S = 32 / c.cfg.G;
       const double per = std::pow((double)N, 3);
+      const double target = std::max(1.0, work[c.wpb] / ((double)sms * c.wpb * pc.chunks_per_warp));
       // a cap on chunk work, but never more than 65,536 chunks per job
       double tj = target;
-      if (js.max_chunk_units > 0) {
-        double job_total = 0.0;
-        for (int mm = 1; mm <= h; ++mm) job_total += (double)binom(h, mm) * std::pow(2.0 * mm, 3);
+      if (js.max_chunk_units > 0)
         tj = std::max(std::min(target, js.max_chunk_units), job_total / (double)js.nparts / 65536.0);
-      }
       uint64_t csz = (uint64_t)std::ceil(tj / per / S) * S;
       csz = std::max<uint64_t>(csz, (uint64_t)S);
       csz = std::min<uint64_t>(csz, (uint64_t)1 << 30);
-      for (uint64_t r0 = 0; r0 < cnt; r0 += csz) {
-        Chunk c;
-        std::memset(&c, 0, sizeof(c));
-        c.rank0 = rlo + r0;
-        c.mask0 = unrank_colex(rlo + r0, m, h);
-        c.count = (uint32_t)std::min<uint64_t>(csz, cnt - r0);
-        c.job = (uint16_t)jb;
-        c.m = (uint8_t)m;
-        c.G = (uint8_t)cfg.G;
-        c.ld = (uint8_t)cfg.ld;
-        plan->chunks.push_back(c);
-        cost.push_back((double)c.count * per * (js.loops ? 1.3 : 1.0) / (js.is_real ? 4.0 : 1.0));
+      for (uint64_t r0 = 0; r0 < c.cnt; r0 += csz) {
+        Chunk k;
+        std::memset(&k, 0, sizeof(k));
+        k.rank0 = c.rlo + r0;
+        k.mask0 = unrank_colex(c.rlo + r0, c.m, h);
+        k.count = (uint32_t)std::min<uint64_t>(csz, c.cnt - r0);
+        k.job = (uint16_t)jb;
+        k.m = (uint8_t)c.m;
+        k.G = (uint8_t)c.cfg.G;
+        k.ld = (uint8_t)c.cfg.ld;
+        plan->chunks.push_back(k);
+        cost.push_back((double)k.count * per * (js.loops ? 1.3 : 1.0) / (js.is_real ? 4.0 : 1.0));
+        seg_of.push_back(c.wpb);
       }
-      plan->subsets += (int64_t)cnt;
+      plan->subsets += (int64_t)c.cnt;
     }
     plan->job_begin.push_back((int)plan->chunks.size());
   }
-  plan->order.resize(plan->chunks.size());
-  for (size_t i = 0; i < plan->order.size(); ++i) plan->order[i] = (int)i;
-  std::stable_sort(plan->order.begin(), plan->order.end(),
-                   [&](int a, int b) { return cost[a] > cost[b]; });
+  // segments, most warps per CTA first; inside each, largest chunks first
+  for (int w : {16, 8, 4}) {
+    PlanSeg sg;
+    sg.begin = (int)plan->order.size();
+    for (size_t i = 0; i < plan->chunks.size(); ++i)
+      if (seg_of[i] == w) plan->order.push_back((int)i);
+    sg.end = (int)plan->order.size();
+    if (sg.end == sg.begin) continue;
+    std::stable_sort(plan->order.begin() + sg.begin, plan->order.end(),
+                     [&](int a, int b) { return cost[a] > cost[b]; });
+    sg.wpb = w;
+    sg.warp_bytes = warp_bytes_for(w);
+    plan->segs.push_back(sg);
+  }
+  plan->wpb = plan->segs.empty() ? pc.wpb : plan->segs[0].wpb;
+  plan->warp_bytes = warp_bytes_for(plan->wpb);
   return HAF_OK;
 }
 
@@ -171,6 +215,10 @@ struct DevPlan {
   int nchunks = 0;
   int njobs = 0;
   int64_t subsets = 0;
+  int kind = kKindC128;
+  int wpb = kWarpsPerBlock;  // first segment's
+  int warp_bytes = kWarpBytes;
+  std::vector<PlanSeg> segs;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -186,7 +234,9 @@ struct Device {
   size_t work_bytes = 0;
   double* host_out = nullptr;  // pinned, grows
   size_t host_out_n = 0;
-  std::map<std::tuple<int, int, int, int64_t, int64_t>, DevPlan> plans;  // (n, loops, real, part, nparts)
+  // (n, loops, real, prec, part, nparts, warps per CTA, chunks per warp)
+  std::map<std::tuple<int, int, int, int, int64_t, int64_t, int, int>, DevPlan> plans;
+  std::map<std::tuple<int, int, int, int>, PlanCfg> tuned;  // (n, loops, real, prec) -> launch shape
 };
 
 std::mutex g_mu;
@@ -219,6 +269,10 @@ int upload_plan(const Plan& p, cudaStream_t st, DevPlan* dp) {
   dp->nchunks = (int)p.chunks.size();
   dp->njobs = (int)p.job_begin.size() - 1;
   dp->subsets = p.subsets;
+  dp->kind = p.kind;
+  dp->wpb = p.wpb;
+  dp->warp_bytes = p.warp_bytes;
+  dp->segs = p.segs;
   HAF_CUDA(cudaMalloc(&dp->chunks, std::max<size_t>(1, p.chunks.size()) * sizeof(Chunk)));
   HAF_CUDA(cudaMalloc(&dp->order, std::max<size_t>(1, p.order.size()) * sizeof(int)));
   HAF_CUDA(cudaMalloc(&dp->job_begin, p.job_begin.size() * sizeof(int)));
@@ -239,9 +293,22 @@ void free_plan(DevPlan* dp) {
   *dp = DevPlan();
 }
 
-int cached_plan(Device* d, int n, int loops, int is_real, DevPlan** out, int64_t part = 0,
-                int64_t nparts = 1) {
-  auto key = std::make_tuple(n, loops, is_real, part, nparts);
+// Launch shape for one matrix: the tuned one if haf_tune (or haf_tune_set)
+// recorded one for this (n, kind), else the default: 4 warps per CTA for
+// FP64 (one warp per SM sub-partition saturates the DFMA pipe), 8 for the
+// FP32 mode (more warps hide shared-memory latency), 8 chunks per warp.
+PlanCfg plan_cfg(Device* d, int n, int loops, int is_real, int prec) {
+  auto it = d->tuned.find(std::make_tuple(n, loops, is_real, prec));
+  if (it != d->tuned.end()) return it->second;
+  PlanCfg c;
+  c.wpb = (prec == kPrecF32) ? 8 : kWarpsPerBlock;
+  return c;
+}
+
+int cached_plan(Device* d, int n, int loops, int is_real, int prec, DevPlan** out, int64_t part = 0,
+                int64_t nparts = 1, const PlanCfg* force = nullptr) {
+  const PlanCfg pc = force ? *force : plan_cfg(d, n, loops, is_real, prec);
+  auto key = std::make_tuple(n, loops, is_real, prec, part, nparts, pc.wpb, pc.chunks_per_warp);
   auto it = d->plans.find(key);
   if (it != d->plans.end()) {
     *out = &it->second;
@@ -251,7 +318,8 @@ int cached_plan(Device* d, int n, int loops, int is_real, DevPlan** out, int64_t
   JobSpec js{n, loops, is_real};
   js.part = part;
   js.nparts = nparts;
-  int rc = build_plan({js}, d->sms * kWarpsPerBlock, &p);
+  js.prec = prec;
+  int rc = build_plan({js}, d->sms, pc, &p);
   if (rc) return rc;
   DevPlan dp;
   rc = upload_plan(p, d->stream, &dp);
@@ -304,24 +372,28 @@ int ensure_host_out(Device* d, size_t ndoubles) {
 // Enqueue prep + subset kernel + finalize for a plan whose jobs' At/diag
 // already sit in device memory.
 int enqueue(Device* d, const DevPlan& dp, const std::vector<Job>& jobs_host, Job* jobs_dev,
-            double* partials, int* counter, double* d_out, int is_real, cudaStream_t st,
+            double* partials, int* counter, double* d_out, cudaStream_t st,
             const uint64_t* masks = nullptr, double* terms_out = nullptr) {
   HAF_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host.data(), jobs_host.size() * sizeof(Job),
                            cudaMemcpyHostToDevice, st));
-  HAF_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
-  KernelArgs a;
-  a.jobs = jobs_dev;
-  a.chunks = dp.chunks;
-  a.order = dp.order;
-  a.nchunks = dp.nchunks;
-  a.counter = counter;
-  a.partials = partials;
-  a.tables = d->tables;
-  a.masks = masks;
-  a.terms_out = terms_out;
-  a.warp_bytes = kWarpBytes;
-  const int grid = std::max(1, std::min(d->sms, (dp.nchunks + kWarpsPerBlock - 1) / kWarpsPerBlock));
-  HAF_CUDA(launch_subsets(a, is_real, grid, st));
+  HAF_CUDA(cudaMemsetAsync(counter, 0, sizeof(int) * std::max<size_t>(1, dp.segs.size()), st));
+  // one launch per segment (counter si for segment si)
+  for (size_t si = 0; si < dp.segs.size(); ++si) {
+    const PlanSeg& sg = dp.segs[si];
+    KernelArgs a;
+    a.jobs = jobs_dev;
+    a.chunks = dp.chunks;
+    a.order = dp.order + sg.begin;
+    a.nchunks = sg.end - sg.begin;
+    a.counter = counter + si;
+    a.partials = partials;
+    a.tables = d->tables;
+    a.masks = masks;
+    a.terms_out = terms_out;
+    a.warp_bytes = sg.warp_bytes;
+    const int grid = std::max(1, std::min(d->sms, (a.nchunks + sg.wpb - 1) / sg.wpb));
+    HAF_CUDA(launch_subsets(a, dp.kind, sg.wpb, grid, st));
+  }
   if (!terms_out) HAF_CUDA(launch_finalize(partials, dp.job_begin, dp.njobs, d_out, st));
   return HAF_OK;
 }
@@ -331,9 +403,10 @@ double now_s() {
 }
 
 // Synchronous single matrix from host memory.
-int run_single(const double* A, int64_t n64, int loops, int is_real, double* out, haf_info* info) {
+int run_single(const double* A, int64_t n64, int loops, int is_real, int prec, double* out, haf_info* info) {
   const double t0 = now_s();
   if (n64 < 0 || n64 > kMaxN) return fail(HAF_EINVAL, "n out of range");
+  if (prec == kPrecF32 && n64 > HAF_FP32_MAX_N) return fail(HAF_EINVAL, "FP32 mode: n above HAF_FP32_MAX_N");
   if (!out || (n64 > 0 && !A)) return fail(HAF_EINVAL, "null pointer");
   int n = (int)n64;
   const int elem = is_real ? 1 : 2;
@@ -375,7 +448,7 @@ int run_single(const double* A, int64_t n64, int loops, int is_real, double* out
   int rc = get_device(&d);
   if (rc) return rc;
   DevPlan* dp;
-  rc = cached_plan(d, n, loops, is_real, &dp);
+  rc = cached_plan(d, n, loops, is_real, prec, &dp);
   if (rc) return rc;
   WsLayout w = ws_layout(n, dp->nchunks);
   const size_t jobs_off = w.total;
@@ -395,12 +468,12 @@ int run_single(const double* A, int64_t n64, int loops, int is_real, double* out
   HAF_CUDA(launch_prep(Ad, n, is_real, At, diag, st));
   std::vector<Job> jobs{Job{At, diag, n, loops}};
   rc = enqueue(d, *dp, jobs, (Job*)(base + jobs_off), (double*)(base + w.partials),
-               (int*)(base + w.counter), (double*)(base + out_off), is_real, st);
+               (int*)(base + w.counter), (double*)(base + out_off), st);
   if (rc) return rc;
   HAF_CUDA(cudaMemcpyAsync(d->host_out, base + out_off, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
   HAF_CUDA(cudaStreamSynchronize(st));
   const double* o = d->host_out;
-  write(o[0] + o[2], o[1] + o[3], o[2], o[3], o[4], dp->subsets, 3);
+  write(o[0] + o[2], o[1] + o[3], o[2], o[3], o[4], dp->subsets, 2 + (int64_t)dp->segs.size());
   return HAF_OK;
 }
 
@@ -408,10 +481,11 @@ int run_single(const double* A, int64_t n64, int loops, int is_real, double* out
 // synchronous): writes the raw record {re_hi, im_hi, re_lo, im_lo, abs_sum}
 // of that part's signed terms.  n = 0 and odd n follow the conventions of
 // the whole-matrix entry points (the value goes to part 0).
-int run_part(const double* A, int64_t n64, int loops, int is_real, int64_t part, int64_t nparts,
+int run_part(const double* A, int64_t n64, int loops, int is_real, int prec, int64_t part, int64_t nparts,
              double* rec, haf_info* info) {
   const double t0 = now_s();
   if (n64 < 0 || n64 > kMaxN) return fail(HAF_EINVAL, "n out of range");
+  if (prec == kPrecF32 && n64 > HAF_FP32_MAX_N) return fail(HAF_EINVAL, "FP32 mode: n above HAF_FP32_MAX_N");
   if (nparts < 1 || part < 0 || part >= nparts) return fail(HAF_EINVAL, "part must satisfy 0 <= part < nparts");
   if (!rec || (n64 > 0 && !A)) return fail(HAF_EINVAL, "null pointer");
   int n = (int)n64;
@@ -441,7 +515,7 @@ int run_part(const double* A, int64_t n64, int loops, int is_real, int64_t part,
   int rc = get_device(&d);
   if (rc) return rc;
   DevPlan* dp;
-  rc = cached_plan(d, n, loops, is_real, &dp, part, nparts);
+  rc = cached_plan(d, n, loops, is_real, prec, &dp, part, nparts);
   if (rc) return rc;
   WsLayout w = ws_layout(n, dp->nchunks);
   const size_t jobs_off = w.total, out_off = jobs_off + 256, stage_off = out_off + 256;
@@ -462,13 +536,13 @@ int run_part(const double* A, int64_t n64, int loops, int is_real, int64_t part,
   } else {
     std::vector<Job> jobs{Job{At, diag, n, loops}};
     rc = enqueue(d, *dp, jobs, (Job*)(base + jobs_off), (double*)(base + w.partials), (int*)(base + w.counter),
-                 (double*)(base + out_off), is_real, st);
+                 (double*)(base + out_off), st);
     if (rc) return rc;
     HAF_CUDA(cudaMemcpyAsync(d->host_out, base + out_off, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
     HAF_CUDA(cudaStreamSynchronize(st));
     std::memcpy(rec, d->host_out, 5 * sizeof(double));
   }
-  if (info) *info = haf_info{rec[4], {rec[2], rec[3]}, dp->subsets, now_s() - t0, dp->nchunks ? 3 : 1};
+  if (info) *info = haf_info{rec[4], {rec[2], rec[3]}, dp->subsets, now_s() - t0, dp->nchunks ? 2 + (int64_t)dp->segs.size() : 1};
   return HAF_OK;
 }
 
@@ -484,6 +558,10 @@ struct BatchPlan {
   std::vector<int> ns;  // sizes after padding (all even, >= 2)
   int loops = -1;
   int is_real = 0;
+  int prec = kPrecF64;
+  PlanCfg cfg;      // requested launch shape
+  int wpb = kWarpsPerBlock;  // planned warps per CTA (first launch)
+  int nsegs = 1;             // subset-kernel launches per replay
   char* dbuf = nullptr;
   double* h_in = nullptr;   // pinned staging of the inputs
   double* h_out = nullptr;  // pinned results, 5 per job
@@ -504,17 +582,26 @@ void free_batch(BatchPlan* b) {
 
 std::map<int, BatchPlan> g_batch;  // device -> last batch plan
 
-int build_batch(Device* d, const std::vector<int>& ns, int loops, int is_real, BatchPlan* b) {
+int build_batch(Device* d, const std::vector<int>& ns, int loops, int is_real, int prec, const PlanCfg& pc,
+                BatchPlan* b) {
   free_batch(b);
   b->ns = ns;
   b->loops = loops;
   b->is_real = is_real;
+  b->prec = prec;
+  b->cfg = pc;
   const int njobs = (int)ns.size();
   std::vector<JobSpec> specs;
-  for (int n : ns) specs.push_back(JobSpec{n, loops, is_real});
+  for (int n : ns) {
+    JobSpec js{n, loops, is_real};
+    js.prec = prec;
+    specs.push_back(js);
+  }
   Plan p;
-  int rc = build_plan(specs, d->sms * kWarpsPerBlock, &p);
+  int rc = build_plan(specs, d->sms, pc, &p);
   if (rc) return rc;
+  b->wpb = p.wpb;
+  b->nsegs = (int)p.segs.size();
   b->subsets = p.subsets;
   b->nchunks = (int)p.chunks.size();
   const size_t elem = is_real ? 8 : 16;
@@ -575,21 +662,26 @@ int build_batch(Device* d, const std::vector<int>& ns, int loops, int is_real, B
   KernelArgs a;
   a.jobs = (const Job*)(base + jobs_off);
   a.chunks = (const Chunk*)(base + ch_off);
-  a.order = (const int*)(base + ord_off);
-  a.nchunks = b->nchunks;
   a.counter = (int*)(base + cnt_off);
   a.partials = (double*)(base + part_off);
   a.tables = d->tables;
   a.masks = nullptr;
   a.terms_out = nullptr;
-  a.warp_bytes = kWarpBytes;
-  const int grid = std::max(1, std::min(d->sms, (b->nchunks + kWarpsPerBlock - 1) / kWarpsPerBlock));
   cudaGraph_t graph;
   HAF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   cudaError_t ce = cudaMemcpyAsync(base + din_off, b->h_in, in_doubles * 8, cudaMemcpyHostToDevice, st);
   if (ce == cudaSuccess) ce = launch_prep_batch((const double* const*)(base + srcs_off), a.jobs, njobs, is_real, st);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
-  if (ce == cudaSuccess) ce = launch_subsets(a, is_real, grid, st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(a.counter, 0, sizeof(int) * std::max<size_t>(1, p.segs.size()), st);
+  for (size_t si = 0; si < p.segs.size() && ce == cudaSuccess; ++si) {
+    const PlanSeg& sg = p.segs[si];
+    KernelArgs as = a;
+    as.order = (const int*)(base + ord_off) + sg.begin;
+    as.nchunks = sg.end - sg.begin;
+    as.counter = a.counter + si;
+    as.warp_bytes = sg.warp_bytes;
+    const int grid = std::max(1, std::min(d->sms, (as.nchunks + sg.wpb - 1) / sg.wpb));
+    ce = launch_subsets(as, p.kind, sg.wpb, grid, st);
+  }
   if (ce == cudaSuccess) ce = launch_finalize(a.partials, (const int*)(base + jb_off), njobs, (double*)(base + out_off), st);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(b->h_out, base + out_off, (size_t)njobs * 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -602,45 +694,52 @@ int build_batch(Device* d, const std::vector<int>& ns, int loops, int is_real, B
   return HAF_OK;
 }
 
-int run_batched(const double* const* As, const int64_t* ns, int64_t count, int loops, double* outs,
-                haf_info* infos) {
-  const double t0 = now_s();
+// Launch shape of a batch: the tuned one for this size list if
+// haf_batched_tune recorded one; else the single-matrix shape recorded for
+// the batch's largest size (its tiles dominate the shared-memory plan);
+// else 4 warps per CTA (FP64) / 8 (FP32) and 8 chunks per warp.
+std::map<std::tuple<std::vector<int>, int, int>, PlanCfg> g_batch_tuned;  // (sizes, loops, prec)
+
+PlanCfg batch_cfg(Device* d, const std::vector<int>& sizes, int loops, int prec) {
+  auto it = g_batch_tuned.find(std::make_tuple(sizes, loops, prec));
+  if (it != g_batch_tuned.end()) return it->second;
+  const int nmax = sizes.empty() ? 2 : *std::max_element(sizes.begin(), sizes.end());
+  return plan_cfg(d, nmax, loops, 0, prec);
+}
+
+// Sizes after the odd-n convention; trivial entries (n = 0, odd haf) are
+// written to outs/infos directly and left out of `sizes`/`idx`.
+int batch_sizes(const double* const* As, const int64_t* ns, int64_t count, int loops, int prec, double* outs,
+                haf_info* infos, std::vector<int>* sizes, std::vector<int64_t>* idx) {
   if (count < 0 || (count > 0 && (!As || !ns || !outs))) return fail(HAF_EINVAL, "null pointer");
   if (count > 65535) return fail(HAF_EINVAL, "batch too large (max 65535 matrices per call)");
   for (int64_t b = 0; b < count; ++b)
     if (ns[b] < 0 || ns[b] > kMaxN || (ns[b] > 0 && !As[b])) return fail(HAF_EINVAL, "bad matrix in batch");
-  std::vector<int> sizes;
-  std::vector<int64_t> idx;  // job -> batch index
   for (int64_t b = 0; b < count; ++b) {
     const int n = (int)ns[b];
     if (n == 0 || ((n & 1) && !loops)) {
       const double v = (n == 0) ? 1.0 : 0.0;
-      outs[2 * b] = v;
-      outs[2 * b + 1] = 0.0;
+      if (outs) {
+        outs[2 * b] = v;
+        outs[2 * b + 1] = 0.0;
+      }
       if (infos) infos[b] = haf_info{v, {0.0, 0.0}, 0, 0.0, 0};
       continue;
     }
     if (n + (n & 1) > kMaxN) return fail(HAF_EINVAL, "n out of range");
-    sizes.push_back(n + (n & 1));
-    idx.push_back(b);
+    if (prec == kPrecF32 && n + (n & 1) > HAF_FP32_MAX_N) return fail(HAF_EINVAL, "FP32 mode: n above HAF_FP32_MAX_N");
+    sizes->push_back(n + (n & 1));
+    idx->push_back(b);
   }
-  if (sizes.empty()) return HAF_OK;
-  std::lock_guard<std::mutex> lk(g_mu);
-  Device* d;
-  int rc = get_device(&d);
-  if (rc) return rc;
-  BatchPlan& bp = g_batch[d->id];
-  if (bp.ns != sizes || bp.loops != loops || bp.is_real != 0) {
-    rc = build_batch(d, sizes, loops, 0, &bp);
-    if (rc) {
-      free_batch(&bp);
-      return rc;
-    }
-  }
-  // stage the inputs (odd lhaf matrices padded with an isolated looped vertex)
-  for (size_t j = 0; j < sizes.size(); ++j) {
+  return HAF_OK;
+}
+
+// Copy the inputs into the batch's pinned staging (odd lhaf matrices padded
+// with an isolated looped vertex).
+void stage_batch(const BatchPlan& bp, const double* const* As, const int64_t* ns, const std::vector<int64_t>& idx) {
+  for (size_t j = 0; j < bp.ns.size(); ++j) {
     const int64_t b = idx[j];
-    const int n = (int)ns[b], np = sizes[j];
+    const int n = (int)ns[b], np = bp.ns[j];
     double* dst = bp.h_in + bp.in_off[j];
     if (np == n) {
       std::memcpy(dst, As[b], (size_t)n * n * 16);
@@ -650,6 +749,32 @@ int run_batched(const double* const* As, const int64_t* ns, int64_t count, int l
       dst[((size_t)n * np + n) * 2] = 1.0;
     }
   }
+}
+
+int run_batched(const double* const* As, const int64_t* ns, int64_t count, int loops, int prec, double* outs,
+                haf_info* infos) {
+  const double t0 = now_s();
+  if (count > 0 && !outs) return fail(HAF_EINVAL, "null pointer");
+  std::vector<int> sizes;
+  std::vector<int64_t> idx;  // job -> batch index
+  int rc = batch_sizes(As, ns, count, loops, prec, outs, infos, &sizes, &idx);
+  if (rc) return rc;
+  if (sizes.empty()) return HAF_OK;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device* d;
+  rc = get_device(&d);
+  if (rc) return rc;
+  BatchPlan& bp = g_batch[d->id];
+  const PlanCfg pc = batch_cfg(d, sizes, loops, prec);
+  if (bp.ns != sizes || bp.loops != loops || bp.is_real != 0 || bp.prec != prec || bp.cfg.wpb != pc.wpb ||
+      bp.cfg.chunks_per_warp != pc.chunks_per_warp || !bp.exec) {
+    rc = build_batch(d, sizes, loops, 0, prec, pc, &bp);
+    if (rc) {
+      free_batch(&bp);
+      return rc;
+    }
+  }
+  stage_batch(bp, As, ns, idx);
   HAF_CUDA(cudaGraphLaunch(bp.exec, d->stream));
   HAF_CUDA(cudaStreamSynchronize(d->stream));
   const double secs = now_s() - t0;
@@ -660,7 +785,7 @@ int run_batched(const double* const* As, const int64_t* ns, int64_t count, int l
     outs[2 * b + 1] = o[1] + o[3];
     if (infos) {
       const int h = sizes[j] / 2;
-      infos[b] = haf_info{o[4], {o[2], o[3]}, (int64_t)((1ull << h) - 1), secs, 5};
+      infos[b] = haf_info{o[4], {o[2], o[3]}, (int64_t)((1ull << h) - 1), secs, 2 + (int64_t)bp.nsegs};
     }
   }
   return HAF_OK;
@@ -670,22 +795,43 @@ int run_batched(const double* const* As, const int64_t* ns, int64_t count, int l
 
 extern "C" {
 
-int haf_c128(const double* A, int64_t n, double* out, haf_info* info) { return run_single(A, n, 0, 0, out, info); }
-int lhaf_c128(const double* A, int64_t n, double* out, haf_info* info) { return run_single(A, n, 1, 0, out, info); }
-int haf_f64(const double* A, int64_t n, double* out, haf_info* info) { return run_single(A, n, 0, 1, out, info); }
-int lhaf_f64(const double* A, int64_t n, double* out, haf_info* info) { return run_single(A, n, 1, 1, out, info); }
+int haf_c128(const double* A, int64_t n, double* out, haf_info* info) {
+  return run_single(A, n, 0, 0, kPrecF64, out, info);
+}
+int lhaf_c128(const double* A, int64_t n, double* out, haf_info* info) {
+  return run_single(A, n, 1, 0, kPrecF64, out, info);
+}
+int haf_f64(const double* A, int64_t n, double* out, haf_info* info) {
+  return run_single(A, n, 0, 1, kPrecF64, out, info);
+}
+int lhaf_f64(const double* A, int64_t n, double* out, haf_info* info) {
+  return run_single(A, n, 1, 1, kPrecF64, out, info);
+}
+
+int haf_eval(const double* A, int64_t n, uint32_t flags, double* out, haf_info* info) {
+  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL | HAF_FLAG_FP32)) return fail(HAF_EINVAL, "haf_eval: unknown flags");
+  return run_single(A, n, (flags & HAF_FLAG_LOOPS) ? 1 : 0, (flags & HAF_FLAG_REAL) ? 1 : 0,
+                    (flags & HAF_FLAG_FP32) ? kPrecF32 : kPrecF64, out, info);
+}
 
 int haf_c128_batched(const double* const* As, const int64_t* ns, int64_t count, double* outs, haf_info* infos) {
-  return run_batched(As, ns, count, 0, outs, infos);
+  return run_batched(As, ns, count, 0, kPrecF64, outs, infos);
 }
 int lhaf_c128_batched(const double* const* As, const int64_t* ns, int64_t count, double* outs, haf_info* infos) {
-  return run_batched(As, ns, count, 1, outs, infos);
+  return run_batched(As, ns, count, 1, kPrecF64, outs, infos);
+}
+int haf_batched(const double* const* As, const int64_t* ns, int64_t count, uint32_t flags, double* outs,
+                haf_info* infos) {
+  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_FP32)) return fail(HAF_EINVAL, "haf_batched: unknown flags");
+  return run_batched(As, ns, count, (flags & HAF_FLAG_LOOPS) ? 1 : 0, (flags & HAF_FLAG_FP32) ? kPrecF32 : kPrecF64,
+                     outs, infos);
 }
 
 int haf_part(const double* A, int64_t n, uint32_t flags, int64_t part, int64_t nparts, double* rec,
              haf_info* info) {
-  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL)) return fail(HAF_EINVAL, "haf_part: unknown flags");
-  return run_part(A, n, (flags & HAF_FLAG_LOOPS) ? 1 : 0, (flags & HAF_FLAG_REAL) ? 1 : 0, part, nparts, rec, info);
+  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL | HAF_FLAG_FP32)) return fail(HAF_EINVAL, "haf_part: unknown flags");
+  return run_part(A, n, (flags & HAF_FLAG_LOOPS) ? 1 : 0, (flags & HAF_FLAG_REAL) ? 1 : 0,
+                  (flags & HAF_FLAG_FP32) ? kPrecF32 : kPrecF64, part, nparts, rec, info);
 }
 
 int haf_part_subsets(int64_t n, int64_t part, int64_t nparts, int64_t* subsets) {
@@ -699,6 +845,29 @@ int haf_part_subsets(int64_t n, int64_t part, int64_t nparts, int64_t* subsets) 
     total += (int64_t)(hi - lo);
   }
   *subsets = total;
+  return HAF_OK;
+}
+
+int haf_plan_stats(int64_t n, uint32_t flags, int32_t warps_per_block, int32_t chunks_per_warp, int32_t sms,
+                   int64_t* out) {
+  if (n < 2 || n > kMaxN || (n & 1) || !out || sms < 1 || sms > 1024)
+    return fail(HAF_EINVAL, "haf_plan_stats: bad arguments");
+  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL | HAF_FLAG_FP32)) return fail(HAF_EINVAL, "haf_plan_stats: unknown flags");
+  JobSpec js{(int)n, (flags & HAF_FLAG_LOOPS) ? 1 : 0, (flags & HAF_FLAG_REAL) ? 1 : 0};
+  js.prec = (flags & HAF_FLAG_FP32) ? kPrecF32 : kPrecF64;
+  PlanCfg pc;
+  pc.wpb = warps_per_block;
+  pc.chunks_per_warp = chunks_per_warp;
+  Plan p;
+  const int rc = build_plan({js}, sms, pc, &p);
+  if (rc) return rc;
+  for (int k = 0; k < 8; ++k) out[k] = 0;
+  out[0] = (int64_t)p.chunks.size();
+  out[1] = (int64_t)p.segs.size();
+  for (size_t si = 0; si < p.segs.size() && si < 3; ++si) {
+    out[2 + si] = p.segs[si].wpb;
+    for (int q = p.segs[si].begin; q < p.segs[si].end; ++q) out[5 + si] += p.chunks[p.order[q]].count;
+  }
   return HAF_OK;
 }
 
@@ -730,11 +899,14 @@ int haf_combine(const double* recs, int64_t nparts, double* out) {
 
 size_t haf_workspace_bytes(int64_t n, uint32_t flags) {
   if (n < 2 || n > kMaxN || (n & 1)) return 0;
+  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL | HAF_FLAG_FP32)) return 0;
+  const int prec = (flags & HAF_FLAG_FP32) ? kPrecF32 : kPrecF64;
+  if (prec == kPrecF32 && n > HAF_FP32_MAX_N) return 0;
   std::lock_guard<std::mutex> lk(g_mu);
   Device* d;
   if (get_device(&d)) return 0;
   DevPlan* dp;
-  if (cached_plan(d, (int)n, (flags & HAF_FLAG_LOOPS) ? 1 : 0, (flags & HAF_FLAG_REAL) ? 1 : 0, &dp)) return 0;
+  if (cached_plan(d, (int)n, (flags & HAF_FLAG_LOOPS) ? 1 : 0, (flags & HAF_FLAG_REAL) ? 1 : 0, prec, &dp)) return 0;
   return ws_layout((int)n, dp->nchunks).total + 256;
 }
 
@@ -743,14 +915,16 @@ int haf_launch(const double* dA, int64_t n, uint32_t flags, double* d_out, void*
   if (n < 2 || n > kMaxN || (n & 1)) return fail(HAF_EINVAL, "haf_launch: n must be even, 2..HAF_MAX_N");
   if (!dA || !d_out || !d_work) return fail(HAF_EINVAL, "haf_launch: null pointer");
   if (((uintptr_t)d_work & 255) != 0) return fail(HAF_EINVAL, "haf_launch: workspace not 256-byte aligned");
-  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL)) return fail(HAF_EINVAL, "haf_launch: unknown flags");
+  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL | HAF_FLAG_FP32)) return fail(HAF_EINVAL, "haf_launch: unknown flags");
   const int loops = (flags & HAF_FLAG_LOOPS) ? 1 : 0, is_real = (flags & HAF_FLAG_REAL) ? 1 : 0;
+  const int prec = (flags & HAF_FLAG_FP32) ? kPrecF32 : kPrecF64;
+  if (prec == kPrecF32 && n > HAF_FP32_MAX_N) return fail(HAF_EINVAL, "FP32 mode: n above HAF_FP32_MAX_N");
   std::lock_guard<std::mutex> lk(g_mu);
   Device* d;
   int rc = get_device(&d);
   if (rc) return rc;
   DevPlan* dp;
-  rc = cached_plan(d, (int)n, loops, is_real, &dp);
+  rc = cached_plan(d, (int)n, loops, is_real, prec, &dp);
   if (rc) return rc;
   WsLayout w = ws_layout((int)n, dp->nchunks);
   if (ws_bytes < w.total + 256) return fail(HAF_ESMALL, "haf_launch: workspace too small");
@@ -761,15 +935,24 @@ int haf_launch(const double* dA, int64_t n, uint32_t flags, double* d_out, void*
   HAF_CUDA(launch_prep(dA, (int)n, is_real, At, diag, st));
   std::vector<Job> jobs{Job{At, diag, (int)n, loops}};
   return enqueue(d, *dp, jobs, (Job*)(base + w.total), (double*)(base + w.partials), (int*)(base + w.counter),
-                 d_out, is_real, st);
+                 d_out, st);
 }
 
 int haf_terms_c128(const double* A, int64_t n64, int loops, const uint64_t* masks, int64_t count, double* terms) {
-  if (n64 < 2 || n64 > kMaxN || (n64 & 1)) return fail(HAF_EINVAL, "haf_terms_c128: n must be even, 2..HAF_MAX_N");
-  if (!A || (count > 0 && (!masks || !terms)) || count < 0) return fail(HAF_EINVAL, "haf_terms_c128: bad arguments");
+  return haf_terms(A, n64, loops ? HAF_FLAG_LOOPS : 0u, masks, count, terms);
+}
+
+int haf_terms(const double* A, int64_t n64, uint32_t flags, const uint64_t* masks, int64_t count, double* terms) {
+  if (n64 < 2 || n64 > kMaxN || (n64 & 1)) return fail(HAF_EINVAL, "haf_terms: n must be even, 2..HAF_MAX_N");
+  if (!A || (count > 0 && (!masks || !terms)) || count < 0) return fail(HAF_EINVAL, "haf_terms: bad arguments");
+  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_FP32)) return fail(HAF_EINVAL, "haf_terms: unknown flags");
+  const int loops = (flags & HAF_FLAG_LOOPS) ? 1 : 0;
+  const int prec = (flags & HAF_FLAG_FP32) ? kPrecF32 : kPrecF64;
+  if (prec == kPrecF32 && n64 > HAF_FP32_MAX_N) return fail(HAF_EINVAL, "FP32 mode: n above HAF_FP32_MAX_N");
+  const int kind = kernel_kind(0, prec);
   const int n = (int)n64, h = n / 2;
   for (int64_t i = 0; i < count; ++i)
-    if (masks[i] >> h) return fail(HAF_EINVAL, "haf_terms_c128: mask has bits beyond n/2");
+    if (masks[i] >> h) return fail(HAF_EINVAL, "haf_terms: mask has bits beyond n/2");
   if (count == 0) return HAF_OK;
   // sort subsets by size; each size becomes chunks of one group-round each
   std::vector<int64_t> perm(count);
@@ -791,7 +974,7 @@ int haf_terms_c128(const double* A, int64_t n64, int loops, const uint64_t* mask
       continue;
     }
     SizeCfg cfg;
-    if (!choose_cfg(2 * m, h, 16, &cfg)) return fail(HAF_EINVAL, "haf_terms_c128: size too large");
+    if (!choose_cfg(2 * m, h, kind, kWarpBytes, &cfg)) return fail(HAF_EINVAL, "haf_terms: size too large");
     const int S = 32 / cfg.G;
     for (int64_t r = i; r < e; r += 4 * S) {
       Chunk c;
@@ -808,6 +991,10 @@ int haf_terms_c128(const double* A, int64_t n64, int loops, const uint64_t* mask
   p.job_begin.push_back((int)p.chunks.size());
   p.order.resize(p.chunks.size());
   for (size_t q = 0; q < p.order.size(); ++q) p.order[q] = (int)q;
+  p.kind = kind;
+  p.wpb = kWarpsPerBlock;
+  p.warp_bytes = kWarpBytes;
+  p.segs.assign(1, PlanSeg{0, (int)p.chunks.size(), kWarpsPerBlock, kWarpBytes});
   std::vector<double> res((size_t)count * 2, 0.0);
   if (!p.chunks.empty()) {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -840,10 +1027,14 @@ int haf_terms_c128(const double* A, int64_t n64, int loops, const uint64_t* mask
     dp.job_begin = (int*)(base + jb_off);
     dp.nchunks = (int)p.chunks.size();
     dp.njobs = 1;
+    dp.kind = p.kind;
+    dp.wpb = p.wpb;
+    dp.warp_bytes = p.warp_bytes;
+    dp.segs = p.segs;
     HAF_CUDA(cudaMemcpyAsync(dp.chunks, p.chunks.data(), p.chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice, st));
     HAF_CUDA(cudaMemcpyAsync(dp.order, p.order.data(), p.order.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     std::vector<Job> jobs{Job{(double*)(base + at_off), (double*)(base + dg_off), n, loops ? 1 : 0}};
-    rc = enqueue(d, dp, jobs, (Job*)(base + job_off), nullptr, (int*)(base + cnt_off), nullptr, 0, st,
+    rc = enqueue(d, dp, jobs, (Job*)(base + job_off), nullptr, (int*)(base + cnt_off), nullptr, st,
                  (const uint64_t*)(base + mk_off), (double*)(base + tm_off));
     if (rc) return rc;
     std::vector<double> tmp((size_t)count * 2);
@@ -855,6 +1046,221 @@ int haf_terms_c128(const double* A, int64_t n64, int loops, const uint64_t* mask
     }
   }
   std::memcpy(terms, res.data(), res.size() * sizeof(double));
+  return HAF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner.  The launch shape of a plan -- warps per CTA (which sets the
+// shared-memory slice per warp, hence the lanes per subset G and the
+// subsets per CTA) and the chunk granularity -- is picked by timing every
+// candidate on the device and keeping the fastest.  Inputs are synthetic
+// (the work does not depend on the matrix entries); results are recorded
+// per device and used by every later call with the same key.
+// ---------------------------------------------------------------------------
+namespace {
+
+const int kTuneWpb[3] = {4, 8, 16};
+const int kTuneCpw[4] = {2, 4, 8, 16};
+
+// Deterministic symmetric test matrix for timing (entries in [-1, 1)).
+std::vector<double> tune_matrix(int n, int is_real) {
+  const int elem = is_real ? 1 : 2;
+  std::vector<double> A((size_t)n * n * elem);
+  uint64_t x = 0x9e3779b97f4a7c15ull;
+  for (int i = 0; i < n; ++i)
+    for (int j = i; j < n; ++j)
+      for (int c = 0; c < elem; ++c) {
+        x ^= x << 13;
+        x ^= x >> 7;
+        x ^= x << 17;
+        const double v = (double)(x >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+        A[((size_t)i * n + j) * elem + c] = v;
+        A[((size_t)j * n + i) * elem + c] = v;
+      }
+  return A;
+}
+
+// Mean milliseconds of `reps` launches of one plan (after one warm-up).
+int time_plan(Device* d, const DevPlan& dp, int n, int loops, const double* Ad, int is_real, char* base, int reps,
+              double* ms_out) {
+  WsLayout w = ws_layout(n, dp.nchunks);
+  cudaStream_t st = d->stream;
+  double* At = (double*)(base + w.at);
+  double* diag = (double*)(base + w.diag);
+  HAF_CUDA(launch_prep(Ad, n, is_real, At, diag, st));
+  std::vector<Job> jobs{Job{At, diag, n, loops}};
+  cudaEvent_t e0, e1;
+  HAF_CUDA(cudaEventCreate(&e0));
+  HAF_CUDA(cudaEventCreate(&e1));
+  int rc = HAF_OK;
+  for (int r = 0; r <= reps && rc == HAF_OK; ++r) {
+    if (r == 1) cudaEventRecord(e0, st);
+    rc = enqueue(d, dp, jobs, (Job*)(base + w.total), (double*)(base + w.partials), (int*)(base + w.counter),
+                 (double*)(base + w.total + 256), st);
+  }
+  cudaEventRecord(e1, st);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (rc == HAF_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (e != cudaSuccess) return fail(HAF_ECUDA, std::string("tune timing: ") + cudaGetErrorString(e));
+  *ms_out = ms / reps;
+  return HAF_OK;
+}
+
+bool same_cfg(const PlanCfg& a, const PlanCfg& b) {
+  return a.wpb == b.wpb && a.chunks_per_warp == b.chunks_per_warp;
+}
+
+}  // namespace
+
+extern "C" {
+
+int haf_tune(int64_t n64, uint32_t flags, int32_t reps, haf_tune_result* out) {
+  if (n64 < 2 || n64 > kMaxN || (n64 & 1)) return fail(HAF_EINVAL, "haf_tune: n must be even, 2..HAF_MAX_N");
+  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL | HAF_FLAG_FP32)) return fail(HAF_EINVAL, "haf_tune: unknown flags");
+  if (reps < 1 || reps > 100 || !out) return fail(HAF_EINVAL, "haf_tune: reps must be 1..100, out non-null");
+  const int n = (int)n64, loops = (flags & HAF_FLAG_LOOPS) ? 1 : 0, is_real = (flags & HAF_FLAG_REAL) ? 1 : 0;
+  const int prec = (flags & HAF_FLAG_FP32) ? kPrecF32 : kPrecF64;
+  if (prec == kPrecF32 && n > HAF_FP32_MAX_N) return fail(HAF_EINVAL, "FP32 mode: n above HAF_FP32_MAX_N");
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device* d;
+  int rc = get_device(&d);
+  if (rc) return rc;
+  const auto key = std::make_tuple(n, loops, is_real, prec);
+  d->tuned.erase(key);
+  const PlanCfg def = plan_cfg(d, n, loops, is_real, prec);
+  // plans of every feasible candidate (a shape the planner had to lower is skipped)
+  std::vector<std::pair<PlanCfg, DevPlan*>> cands;
+  size_t ws = 0;
+  for (int wpb : kTuneWpb)
+    for (int cpw : kTuneCpw) {
+      PlanCfg c;
+      c.wpb = wpb;
+      c.chunks_per_warp = cpw;
+      DevPlan* dp;
+      rc = cached_plan(d, n, loops, is_real, prec, &dp, 0, 1, &c);
+      if (rc) return rc;
+      if (dp->wpb != wpb) continue;
+      cands.push_back({c, dp});
+      ws = std::max(ws, ws_layout(n, dp->nchunks).total + 512);
+    }
+  const size_t abytes = (size_t)n * n * (is_real ? 8 : 16);
+  rc = ensure_work(d, ws + align256(abytes));
+  if (rc) return rc;
+  char* base = (char*)d->work;
+  double* Ad = (double*)(base + ws);
+  const std::vector<double> A = tune_matrix(n, is_real);
+  HAF_CUDA(cudaMemcpyAsync(Ad, A.data(), abytes, cudaMemcpyHostToDevice, d->stream));
+  double best = 1e300, ms_def = -1.0;
+  PlanCfg best_cfg = def;
+  for (auto& c : cands) {
+    double ms;
+    rc = time_plan(d, *c.second, n, loops, Ad, is_real, base, reps, &ms);
+    if (rc) return rc;
+    if (same_cfg(c.first, def)) ms_def = ms;
+    if (ms < best) {
+      best = ms;
+      best_cfg = c.first;
+    }
+  }
+  d->tuned[key] = best_cfg;
+  out->warps_per_block = best_cfg.wpb;
+  out->chunks_per_warp = best_cfg.chunks_per_warp;
+  out->ms = best;
+  out->ms_default = ms_def;
+  out->candidates = (int32_t)cands.size();
+  return HAF_OK;
+}
+
+int haf_tune_set(int64_t n64, uint32_t flags, int32_t warps_per_block, int32_t chunks_per_warp) {
+  if (n64 < 2 || n64 > kMaxN || (n64 & 1)) return fail(HAF_EINVAL, "haf_tune_set: n must be even, 2..HAF_MAX_N");
+  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL | HAF_FLAG_FP32)) return fail(HAF_EINVAL, "haf_tune_set: unknown flags");
+  if ((warps_per_block != 4 && warps_per_block != 8 && warps_per_block != 16) || chunks_per_warp < 1 ||
+      chunks_per_warp > 64)
+    return fail(HAF_EINVAL, "haf_tune_set: warps per CTA must be 4, 8 or 16 and chunks per warp 1..64");
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device* d;
+  int rc = get_device(&d);
+  if (rc) return rc;
+  PlanCfg c;
+  c.wpb = warps_per_block;
+  c.chunks_per_warp = chunks_per_warp;
+  d->tuned[std::make_tuple((int)n64, (flags & HAF_FLAG_LOOPS) ? 1 : 0, (flags & HAF_FLAG_REAL) ? 1 : 0,
+                           (flags & HAF_FLAG_FP32) ? kPrecF32 : kPrecF64)] = c;
+  return HAF_OK;
+}
+
+int haf_batched_tune(const double* const* As, const int64_t* ns, int64_t count, uint32_t flags, int32_t reps,
+                     haf_tune_result* out) {
+  if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_FP32)) return fail(HAF_EINVAL, "haf_batched_tune: unknown flags");
+  if (reps < 1 || reps > 100 || !out) return fail(HAF_EINVAL, "haf_batched_tune: reps must be 1..100, out non-null");
+  const int loops = (flags & HAF_FLAG_LOOPS) ? 1 : 0, prec = (flags & HAF_FLAG_FP32) ? kPrecF32 : kPrecF64;
+  std::vector<double> scratch((size_t)std::max<int64_t>(count, 1) * 2);
+  std::vector<int> sizes;
+  std::vector<int64_t> idx;
+  int rc = batch_sizes(As, ns, count, loops, prec, scratch.data(), nullptr, &sizes, &idx);
+  if (rc) return rc;
+  if (sizes.empty()) return fail(HAF_EINVAL, "haf_batched_tune: no non-trivial matrix in the batch");
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device* d;
+  rc = get_device(&d);
+  if (rc) return rc;
+  const auto key = std::make_tuple(sizes, loops, prec);
+  g_batch_tuned.erase(key);
+  const PlanCfg def = batch_cfg(d, sizes, loops, prec);
+  cudaEvent_t e0, e1;
+  HAF_CUDA(cudaEventCreate(&e0));
+  HAF_CUDA(cudaEventCreate(&e1));
+  double best = 1e300, ms_def = -1.0;
+  PlanCfg best_cfg = def;
+  int ncand = 0;
+  for (int wpb : kTuneWpb)
+    for (int cpw : kTuneCpw) {
+      PlanCfg c;
+      c.wpb = wpb;
+      c.chunks_per_warp = cpw;
+      BatchPlan bp;
+      rc = build_batch(d, sizes, loops, 0, prec, c, &bp);
+      if (rc == HAF_OK && bp.wpb == wpb) {
+        ++ncand;
+        stage_batch(bp, As, ns, idx);
+        cudaError_t e = cudaGraphLaunch(bp.exec, d->stream);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, d->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(bp.exec, d->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, d->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) rc = fail(HAF_ECUDA, std::string("haf_batched_tune: ") + cudaGetErrorString(e));
+        const double m = ms / reps;
+        if (rc == HAF_OK) {
+          if (same_cfg(c, def)) ms_def = m;
+          if (m < best) {
+            best = m;
+            best_cfg = c;
+          }
+        }
+      }
+      free_batch(&bp);
+      if (rc) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g_batch_tuned[key] = best_cfg;
+  out->warps_per_block = best_cfg.wpb;
+  out->chunks_per_warp = best_cfg.chunks_per_warp;
+  out->ms = best;
+  out->ms_default = ms_def;
+  out->candidates = ncand;
   return HAF_OK;
 }
 
@@ -964,7 +1370,7 @@ int noalloc_setup(int dev, NoAllocDevice** out) {
 // down to 1 (largest tiles first), each cut into chunks of roughly equal
 // work, at most kNaMaxChunks in total.  Returns the chunk count or < 0.
 int noalloc_plan(int n, int is_real, int num_warps) {
-  const int h = n / 2, elem = is_real ? 8 : 16;
+  const int h = n / 2, kind = kernel_kind(is_real, kPrecF64);
   double total = 0.0;
   for (int m = 1; m <= h; ++m) total += (double)binom(h, m) * std::pow(2.0 * m, 3);
   int per_warp = 8;
@@ -975,7 +1381,7 @@ int noalloc_plan(int n, int is_real, int num_warps) {
     for (int m = h; m >= 1 && !over; --m) {
       const int N = 2 * m;
       SizeCfg cfg;
-      if (!choose_cfg(N, h, elem, &cfg)) return fail(HAF_EINVAL, "haf_launch_noalloc: n too large");
+      if (!choose_cfg(N, h, kind, kWarpBytes, &cfg)) return fail(HAF_EINVAL, "haf_launch_noalloc: n too large");
       const int S = 32 / cfg.G;
       const uint64_t cnt = binom(h, m);
       uint64_t csz = (uint64_t)std::ceil(target / std::pow((double)N, 3) / S) * S;
@@ -1048,7 +1454,7 @@ extern "C" int haf_launch_noalloc(const double* dA, int64_t n, uint32_t flags, d
   a.terms_out = nullptr;
   a.warp_bytes = kWarpBytes;
   const int grid = std::max(1, std::min(d->sms, (nc + kWarpsPerBlock - 1) / kWarpsPerBlock));
-  HAF_CUDA(launch_subsets(a, is_real, grid, st));
+  HAF_CUDA(launch_subsets(a, kernel_kind(is_real, kPrecF64), kWarpsPerBlock, grid, st));
   HAF_CUDA(launch_finalize(partials, job_begin, 1, d_out, st));
   return HAF_OK;
 }

@@ -51,6 +51,7 @@ struct KernelArgs {
 #ifndef HAF_WARPS_PER_BLOCK
 #define HAF_WARPS_PER_BLOCK 4
 #endif
+// Warps per CTA of the FP64 default plan and of the server kernel.
 constexpr int kWarpsPerBlock = HAF_WARPS_PER_BLOCK;
 
 // Server: one admitted job as the device sees it (slot-indexed table in
@@ -83,14 +84,38 @@ struct ServerArgs {
   int warp_bytes;
 };
 constexpr int kMaxSmemPerBlock = 232448;  // 227 KiB opt-in on sm_100/sm_103
-constexpr int kWarpBytes = (kMaxSmemPerBlock / kWarpsPerBlock) / 16 * 16;
+// Shared memory owned by each warp when a CTA has `wpb` warps.
+constexpr int warp_bytes_for(int wpb) { return (kMaxSmemPerBlock / wpb) / 16 * 16; }
+constexpr int kWarpBytes = warp_bytes_for(kWarpsPerBlock);
 constexpr int kMaxN = 56;
 
-// Shared-memory bytes one subset needs: tile N x ld, five length-N vectors,
-// six length-(h+1) series and h pair indices.
-inline __host__ __device__ int subset_bytes(int N, int ld, int h, int elem_bytes) {
-  int elems = N * ld + 5 * N + 6 * (h + 1);
-  int b = elems * elem_bytes + 4 * h;
+// Precision of the bulk steps (gather, Householder, loop moments, La Budde).
+// The power series, f(Z) and the subset sum are FP64 in both modes.
+enum { kPrecF64 = 0, kPrecF32 = 1 };
+
+// Kernel kinds: complex128, real float64, complex64 bulk, float32 bulk.
+enum { kKindC128 = 0, kKindF64 = 1, kKindC64 = 2, kKindF32 = 3 };
+inline int kernel_kind(int is_real, int prec) { return (is_real ? 1 : 0) + (prec == kPrecF32 ? 2 : 0); }
+// Bytes of the bulk element (TB) and of the series element (TS) of a kind.
+inline int bulk_elem_bytes(int kind) {
+  static const int b[4] = {16, 8, 8, 4};
+  return b[kind];
+}
+inline int series_elem_bytes(int kind) { return (kind & 1) ? 8 : 16; }
+inline bool kind_mixed(int kind) { return kind >= kKindC64; }
+
+// Shared-memory bytes of one subset.  Same-precision layout: tile N x ld,
+// five length-N vectors, six length-(h+1) series, h pair indices.  Mixed
+// layout: tile, five vectors and two length-(h+1) arrays in the bulk type
+// (subset_bulk_bytes, rounded to 16), then six length-(h+1) series in the
+// series type and the pair indices.
+inline __host__ __device__ int subset_bulk_bytes(int N, int ld, int h, int sb) {
+  const int b = (N * ld + 5 * N + 2 * (h + 1)) * sb;
+  return (b + 15) & ~15;
+}
+inline __host__ __device__ int subset_bytes(int N, int ld, int h, int sb, int ss, bool mixed) {
+  const int b = mixed ? subset_bulk_bytes(N, ld, h, sb) + 6 * (h + 1) * ss + 4 * h
+                      : (N * ld + 5 * N + 6 * (h + 1)) * sb + 4 * h;
   return (b + 15) & ~15;
 }
 
@@ -102,22 +127,42 @@ struct JobSpec {
   int64_t part = 0;  // this job covers part `part` of `nparts` of every size class
   int64_t nparts = 1;
   double max_chunk_units = 0;  // cap on a chunk's work in N^3 units (0: none)
+  int prec = kPrecF64;         // all jobs of one plan share is_real and prec
+};
+// Launch shape of a plan: warps per CTA (4, 8 or 16; size classes whose
+// tiles do not fit that warp slice run in a second launch with fewer warps
+// per CTA) and the chunk granularity (about chunks_per_warp chunks per
+// resident warp, per launch).
+struct PlanCfg {
+  int wpb = kWarpsPerBlock;
+  int chunks_per_warp = 8;
+};
+// One launch of a plan: order[begin, end) run with `wpb` warps per CTA.
+struct PlanSeg {
+  int begin = 0, end = 0;
+  int wpb = kWarpsPerBlock;
+  int warp_bytes = kWarpBytes;
 };
 struct Plan {
-  std::vector<Chunk> chunks;
-  std::vector<int> order;
+  std::vector<Chunk> chunks;   // grouped by job (job_begin), then by size
+  std::vector<int> order;      // launch order: segment by segment, largest chunks first
+  std::vector<PlanSeg> segs;   // most warps per CTA first
   std::vector<int> job_begin;  // njobs + 1
   int64_t subsets = 0;
+  int kind = kKindC128;
+  int wpb = kWarpsPerBlock;    // first segment's (a one-segment plan's) shape
+  int warp_bytes = kWarpBytes;
 };
 uint64_t binom(int a, int b);
 uint64_t unrank_colex(uint64_t rank, int m, int h);
-int build_plan(const std::vector<JobSpec>& jobs, int num_warps, Plan* plan);
+int build_plan(const std::vector<JobSpec>& jobs, int sms, const PlanCfg& cfg, Plan* plan);
 int set_error(int code, const std::string& msg);
 
 // Launchers (haf_kernels.cu).
 cudaError_t launch_prep(const double* A, int n, int is_real, double* At, double* diag,
                         cudaStream_t st);
-cudaError_t launch_subsets(const KernelArgs& a, int is_real, int grid, cudaStream_t st);
+// kind: kKind*; wpb: 4, 8 or 16 warps per CTA (a.warp_bytes = warp_bytes_for(wpb)).
+cudaError_t launch_subsets(const KernelArgs& a, int kind, int wpb, int grid, cudaStream_t st);
 cudaError_t launch_prep_batch(const double* const* srcs, const Job* jobs, int njobs, int is_real,
                               cudaStream_t st);
 cudaError_t launch_finalize(const double* partials, const int* job_begin, int njobs, double* out,

@@ -34,6 +34,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "haf_internal.h"
 
 namespace hafgb {
@@ -45,6 +47,9 @@ constexpr unsigned kFull = 0xffffffffu;
 struct __align__(16) cplx {
   double re, im;
 };
+struct __align__(8) cplxf {
+  float re, im;
+};
 
 // ---------------------------------------------------------------------------
 // Scalar operations for the complex (cplx) and real (double) paths.  Every
@@ -55,6 +60,7 @@ struct Ops;
 
 template <>
 struct Ops<cplx> {
+  using R = double;
   static __device__ __forceinline__ cplx zero() { return cplx{0.0, 0.0}; }
   static __device__ __forceinline__ cplx one() { return cplx{1.0, 0.0}; }
   // acc + a b
@@ -150,6 +156,7 @@ struct Ops<cplx> {
 
 template <>
 struct Ops<double> {
+  using R = double;
   static __device__ __forceinline__ double zero() { return 0.0; }
   static __device__ __forceinline__ double one() { return 1.0; }
   static __device__ __forceinline__ double fma(double a, double b, double acc) { return ::fma(a, b, acc); }
@@ -186,9 +193,124 @@ struct Ops<double> {
   }
 };
 
+// ---------------------------------------------------------------------------
+// FP32 arithmetic for the reduced-precision mode: the gather, the Householder
+// reduction, the loop moments and La Budde's recurrence run in single
+// precision (complex64 / float32); the power series and the subset sum stay
+// in FP64 (see process_chunk).  A single-precision complex multiply-add is
+// four FFMAs, which GB300 retires ~60x faster than DFMAs.
+// ---------------------------------------------------------------------------
+template <>
+struct Ops<cplxf> {
+  using R = float;
+  static __device__ __forceinline__ cplxf zero() { return cplxf{0.f, 0.f}; }
+  static __device__ __forceinline__ cplxf one() { return cplxf{1.f, 0.f}; }
+  static __device__ __forceinline__ cplxf fma(cplxf a, cplxf b, cplxf acc) {
+    acc.re = fmaf(a.re, b.re, acc.re);
+    acc.im = fmaf(a.re, b.im, acc.im);
+    acc.re = fmaf(-a.im, b.im, acc.re);
+    acc.im = fmaf(a.im, b.re, acc.im);
+    return acc;
+  }
+  static __device__ __forceinline__ cplxf fnma(cplxf a, cplxf b, cplxf acc) {
+    acc.re = fmaf(-a.re, b.re, acc.re);
+    acc.im = fmaf(-a.re, b.im, acc.im);
+    acc.re = fmaf(a.im, b.im, acc.re);
+    acc.im = fmaf(-a.im, b.re, acc.im);
+    return acc;
+  }
+  static __device__ __forceinline__ cplxf cfma(cplxf a, cplxf b, cplxf acc) {
+    acc.re = fmaf(a.re, b.re, acc.re);
+    acc.im = fmaf(a.re, b.im, acc.im);
+    acc.re = fmaf(a.im, b.im, acc.re);
+    acc.im = fmaf(-a.im, b.re, acc.im);
+    return acc;
+  }
+  static __device__ __forceinline__ cplxf fnma_cb(cplxf a, cplxf b, cplxf acc) {
+    acc.re = fmaf(-a.re, b.re, acc.re);
+    acc.im = fmaf(-a.im, b.re, acc.im);
+    acc.re = fmaf(-a.im, b.im, acc.re);
+    acc.im = fmaf(a.re, b.im, acc.im);
+    return acc;
+  }
+  static __device__ __forceinline__ cplxf mul(cplxf a, cplxf b) {
+    cplxf r;
+    r.re = a.re * b.re;
+    r.im = a.re * b.im;
+    r.re = fmaf(-a.im, b.im, r.re);
+    r.im = fmaf(a.im, b.re, r.im);
+    return r;
+  }
+  static __device__ __forceinline__ cplxf scale(cplxf a, float s) { return cplxf{a.re * s, a.im * s}; }
+  static __device__ __forceinline__ float abs2(cplxf a) { return fmaf(a.im, a.im, a.re * a.re); }
+  static __device__ __forceinline__ float abs2_acc(cplxf a, float acc) {
+    return fmaf(a.im, a.im, fmaf(a.re, a.re, acc));
+  }
+  static __device__ __forceinline__ cplxf shfl_xor(cplxf a, int o) {
+    return cplxf{__shfl_xor_sync(kFull, a.re, o), __shfl_xor_sync(kFull, a.im, o)};
+  }
+  static __device__ __forceinline__ cplxf add(cplxf a, cplxf b) { return cplxf{a.re + b.re, a.im + b.im}; }
+  static __device__ __forceinline__ cplxf load(const double* p, size_t i) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p) + i);
+    return cplxf{(float)v.x, (float)v.y};
+  }
+  static __device__ __forceinline__ cplx widen(cplxf a) { return cplx{(double)a.re, (double)a.im}; }
+  // the reflector of Ops<cplx>, in single precision
+  static __device__ __forceinline__ void reflector(cplxf x0, float s0, float nrm2, float& c, cplxf& w0,
+                                                   cplxf& alpha) {
+    const bool z0 = __float_as_int(s0) == 0;
+    const bool zz = __float_as_int(nrm2) == 0;
+    const float rn = rsqrtf(nrm2);
+    const float nrm = nrm2 * rn;
+    const float r0 = rsqrtf(s0);
+    const float ax0 = s0 * r0;
+    const float phr = z0 ? 1.f : x0.re * r0;
+    const float phi = z0 ? 0.f : x0.im * r0;
+    const float a0 = z0 ? 0.f : ax0;
+    const float cc = rsqrtf(nrm * (nrm + a0));
+    const float t = cc * (a0 + nrm);
+    c = zz ? 0.f : cc;
+    w0 = zz ? cplxf{0.f, 0.f} : cplxf{phr * t, phi * t};
+    alpha = zz ? x0 : cplxf{-nrm * phr, -nrm * phi};
+  }
+};
+
+template <>
+struct Ops<float> {
+  using R = float;
+  static __device__ __forceinline__ float zero() { return 0.f; }
+  static __device__ __forceinline__ float one() { return 1.f; }
+  static __device__ __forceinline__ float fma(float a, float b, float acc) { return fmaf(a, b, acc); }
+  static __device__ __forceinline__ float fnma(float a, float b, float acc) { return fmaf(-a, b, acc); }
+  static __device__ __forceinline__ float cfma(float a, float b, float acc) { return fmaf(a, b, acc); }
+  static __device__ __forceinline__ float fnma_cb(float a, float b, float acc) { return fmaf(-a, b, acc); }
+  static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+  static __device__ __forceinline__ float scale(float a, float s) { return a * s; }
+  static __device__ __forceinline__ float abs2(float a) { return a * a; }
+  static __device__ __forceinline__ float abs2_acc(float a, float acc) { return fmaf(a, a, acc); }
+  static __device__ __forceinline__ float shfl_xor(float a, int o) { return __shfl_xor_sync(kFull, a, o); }
+  static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+  static __device__ __forceinline__ float load(const double* p, size_t i) { return (float)__ldcg(p + i); }
+  static __device__ __forceinline__ double widen(float a) { return (double)a; }
+  static __device__ __forceinline__ void reflector(float x0, float s0, float nrm2, float& c, float& w0,
+                                                   float& alpha) {
+    const bool zz = __float_as_int(nrm2) == 0;
+    const float rn = rsqrtf(nrm2);
+    const float nrm = nrm2 * rn;
+    const float ax0 = fabsf(x0);
+    const float ph = copysignf(1.f, x0);
+    const float cc = rsqrtf(nrm * (nrm + ax0));
+    c = zz ? 0.f : cc;
+    w0 = zz ? 0.f : ph * (cc * (ax0 + nrm));
+    alpha = zz ? x0 : -nrm * ph;
+    (void)s0;
+  }
+};
+
 // Sum over the G lanes of a group (butterfly: every lane of the group ends
 // with the bitwise-identical sum, since each stage adds a commuting pair).
-__device__ __forceinline__ double group_sum(double x, int G) {
+template <class R>
+__device__ __forceinline__ R group_sum(R x, int G) {
   for (int o = G >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
   return x;
 }
@@ -478,12 +600,13 @@ __device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__
   for (int k = 0; k + 2 < N; ++k) {
     const int k1 = k + 1;
     const int i2 = k + 2 + g;  // this lane's rows below the first reflected entry
-    double sig = 0.0;
+    using R = typename O::R;
+    R sig = R(0);
     for (int i = i2; i < N; i += G) sig = O::abs2_acc(tile[i * ld + k], sig);
     sig = group_sum(sig, G);
     const T x0 = tile[k1 * ld + k];
-    const double s0 = O::abs2(x0);
-    double c;
+    const R s0 = O::abs2(x0);
+    R c;
     T w0, alpha;
     O::reflector(x0, s0, s0 + sig, c, w0, alpha);
     for (int i = i2; i < N; i += G) W[i] = O::scale(tile[i * ld + k], c);
@@ -708,28 +831,50 @@ __device__ void loop_moments_tail(int N, int h, const T* __restrict__ DN, T* U, 
 
 // ---------------------------------------------------------------------------
 // One chunk: ceil(count / S) rounds of S subsets (one per group).
+// TB is the type of the bulk steps (gather, Householder, loop moments, La
+// Budde), TS the type of the power series and of f(Z).  FP64 runs with
+// TB = TS; the FP32 mode runs TB in single precision and widens the
+// characteristic-polynomial coefficients (and loop moments) to FP64 before
+// the series, so only the O(N^3) part loses precision.
+// Per-subset shared-memory layout (subset_bytes in haf_internal.h):
+//   TB: tile N x ld, W, P, TV, VA, VB (N each), DN (h+1)
+//   mixed only: TB loop moments (h+1), then TS DN (h+1) at a 16-byte boundary
+//   TS: GS, AC, U, ES, AC2 (h+1 each); int pos[h]
 // ---------------------------------------------------------------------------
-template <class T>
+template <class TB, class TS>
 __device__ void process_chunk(const Job& job, const Chunk& ch, double* __restrict__ partial_out,
                               const double* __restrict__ tables, const uint64_t* __restrict__ masks,
                               double* __restrict__ terms_out, unsigned char* wbase, int lane) {
-  using O = Ops<T>;
+  using OB = Ops<TB>;
+  using OS = Ops<TS>;
+  constexpr bool kMixed = !std::is_same<TB, TS>::value;
   const int n = job.n, h = n >> 1, m = ch.m, N = 2 * m, G = ch.G, S = 32 / G, ld = ch.ld;
   const int s = lane / G, g = lane - s * G;
   const bool loops = job.loops != 0;
-  const int sub_bytes = subset_bytes(N, ld, h, (int)sizeof(T));
-  T* tile = reinterpret_cast<T*>(wbase + s * sub_bytes);
-  T* W = tile + N * ld;
-  T* P = W + N;
-  T* TV = P + N;
-  T* VA = TV + N;
-  T* VB = VA + N;
-  T* DN = VB + N;
-  T* GS = DN + (h + 1);
-  T* AC = GS + (h + 1);
-  T* U = AC + (h + 1);
-  T* ES = U + (h + 1);
-  T* AC2 = ES + (h + 1);
+  const int sub_bytes = subset_bytes(N, ld, h, (int)sizeof(TB), (int)sizeof(TS), kMixed);
+  unsigned char* base = wbase + s * sub_bytes;
+  TB* tile = reinterpret_cast<TB*>(base);
+  TB* W = tile + N * ld;
+  TB* P = W + N;
+  TB* TV = P + N;
+  TB* VA = TV + N;
+  TB* VB = VA + N;
+  TB* DNb = VB + N;
+  TS* DN;
+  TB* Ub;
+  if constexpr (kMixed) {
+    Ub = DNb + (h + 1);
+    DN = reinterpret_cast<TS*>(base + subset_bulk_bytes(N, ld, h, (int)sizeof(TB)));
+  } else {
+    DN = DNb;
+    Ub = nullptr;
+  }
+  TS* GS = DN + (h + 1);
+  TS* AC = GS + (h + 1);
+  TS* U = AC + (h + 1);
+  TS* ES = U + (h + 1);
+  TS* AC2 = ES + (h + 1);
+  if constexpr (!kMixed) Ub = U;
   int* pos = reinterpret_cast<int*>(AC2 + (h + 1));
   const bool neg = ((h - m) & 1) != 0;
   const bool term_mode = terms_out != nullptr;
@@ -739,8 +884,8 @@ __device__ void process_chunk(const Job& job, const Chunk& ch, double* __restric
   if (!term_mode)
     for (int q = 0; q < s; ++q) mask = next_comb(mask);
 
-  for (uint32_t base = 0; base < ch.count; base += (uint32_t)S) {
-    const uint32_t local = base + (uint32_t)s;
+  for (uint32_t base_r = 0; base_r < ch.count; base_r += (uint32_t)S) {
+    const uint32_t local = base_r + (uint32_t)s;
     const bool valid = local < ch.count;
     uint64_t zmask;
     if (term_mode) {
@@ -760,33 +905,41 @@ __device__ void process_chunk(const Job& job, const Chunk& ch, double* __restric
     for (int e = g; e < N * N; e += G) {
       const int r = e / N, c = e - r * N;
       const int ir = 2 * pos[r >> 1] + (r & 1), ic = 2 * pos[c >> 1] + (c & 1);
-      tile[r * ld + c] = valid ? O::load(job.At, (size_t)ir * n + ic) : O::zero();
+      tile[r * ld + c] = valid ? OB::load(job.At, (size_t)ir * n + ic) : OB::zero();
     }
     if (loops) {
       for (int r = g; r < N; r += G) {
         const int ir = 2 * pos[r >> 1] + (r & 1);
-        const T v = valid ? O::load(job.diag, ir) : O::zero();
+        const TB v = valid ? OB::load(job.diag, ir) : OB::zero();
         VA[r] = v;      // a = v
         VB[r ^ 1] = v;  // b = X v^T
       }
     }
     __syncwarp();
-    householder<T>(tile, ld, N, W, P, TV, VA, VB, DN, loops, g, G);  // DN area as scratch
-    if (loops) loop_moments<T>(tile, ld, N, h, VA, VB, W, TV, U, g, G);
-    labudde<T>(tile, ld, N, h, DN, g, G);
-    if (loops && N < h) loop_moments_tail<T>(N, h, DN, U, g, G);
-    const T f = series<T>(N, h, DN, U, GS, AC, ES, AC2, loops, tables, g, G);
+    householder<TB>(tile, ld, N, W, P, TV, VA, VB, DNb, loops, g, G);  // DN area as scratch
+    if (loops) loop_moments<TB>(tile, ld, N, h, VA, VB, W, TV, Ub, g, G);
+    labudde<TB>(tile, ld, N, h, DNb, g, G);
+    if constexpr (kMixed) {
+      // widen the coefficients (and loop moments) for the FP64 series
+      const int jm = min(N, h);
+      for (int j = g; j <= jm; j += G) DN[j] = OB::widen(DNb[j]);
+      if (loops)
+        for (int k = 1 + g; k <= jm; k += G) U[k] = OB::widen(Ub[k]);
+      __syncwarp();
+    }
+    if (loops && N < h) loop_moments_tail<TS>(N, h, DN, U, g, G);
+    const TS f = series<TS>(N, h, DN, U, GS, AC, ES, AC2, loops, tables, g, G);
     if (term_mode) {
       if (valid && g == 0) {
-        terms_out[2 * (ch.rank0 + local)] = O::re(f);
-        terms_out[2 * (ch.rank0 + local) + 1] = O::im(f);
+        terms_out[2 * (ch.rank0 + local)] = OS::re(f);
+        terms_out[2 * (ch.rank0 + local) + 1] = OS::im(f);
       }
     } else if (valid) {
-      const double fr = neg ? -O::re(f) : O::re(f);
-      const double fi = neg ? -O::im(f) : O::im(f);
+      const double fr = neg ? -OS::re(f) : OS::re(f);
+      const double fi = neg ? -OS::im(f) : OS::im(f);
       dd_add(re_hi, re_lo, fr);
       dd_add(im_hi, im_lo, fi);
-      asum += O::absval(f);
+      asum += OS::absval(f);
     }
     __syncwarp();
   }
@@ -813,8 +966,8 @@ __device__ void process_chunk(const Job& job, const Chunk& ch, double* __restric
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) subset_kernel(KernelArgs args) {
+template <class TB, class TS, int WPB>
+__global__ void __launch_bounds__(32 * WPB, 1) subset_kernel(KernelArgs args) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* wbase = smem + warp * args.warp_bytes;
@@ -826,7 +979,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) subset_kernel(KernelAr
     const int id = args.order[ci];
     const Chunk ch = args.chunks[id];
     const Job job = args.jobs[ch.job];
-    process_chunk<T>(job, ch, args.partials ? args.partials + 5 * (size_t)id : nullptr, args.tables,
+    process_chunk<TB, TS>(job, ch, args.partials ? args.partials + 5 * (size_t)id : nullptr, args.tables,
                      args.masks, args.terms_out, wbase, lane);
   }
 }
@@ -946,7 +1099,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) server_kernel(ServerAr
       continue;
     }
     const long long tc0 = globaltimer();
-    process_chunk<T>(sj.job, ch, sj.partials + 5 * (size_t)ch.aux, a.tables, nullptr, nullptr, wbase, lane);
+    process_chunk<T, T>(sj.job, ch, sj.partials + 5 * (size_t)ch.aux, a.tables, nullptr, nullptr, wbase, lane);
     __threadfence();
     unsigned int prev = 0;
     if (lane == 0) {
@@ -1112,15 +1265,45 @@ __global__ void __launch_bounds__(512) fp64_probe_kernel(double* sink, int iters
 
 }  // namespace
 
+namespace {
+
+template <class TB, class TS, int WPB>
+cudaError_t set_smem_attr() {
+  return cudaFuncSetAttribute(subset_kernel<TB, TS, WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kMaxSmemPerBlock);
+}
+
+template <class TB, class TS>
+cudaError_t set_smem_attrs() {
+  cudaError_t e = set_smem_attr<TB, TS, 4>();
+  if (e == cudaSuccess) e = set_smem_attr<TB, TS, 8>();
+  if (e == cudaSuccess) e = set_smem_attr<TB, TS, 16>();
+  return e;
+}
+
+template <class TB, class TS>
+cudaError_t launch_kind(const KernelArgs& a, int wpb, int grid, cudaStream_t st) {
+  const int smem = a.warp_bytes * wpb;
+  switch (wpb) {
+    case 4: subset_kernel<TB, TS, 4><<<grid, 32 * 4, smem, st>>>(a); break;
+    case 8: subset_kernel<TB, TS, 8><<<grid, 32 * 8, smem, st>>>(a); break;
+    case 16: subset_kernel<TB, TS, 16><<<grid, 32 * 16, smem, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t configure_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(subset_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kWarpBytes * kWarpsPerBlock);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(server_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kWarpBytes * kWarpsPerBlock);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(subset_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kWarpBytes * kWarpsPerBlock);
+  cudaError_t e = set_smem_attrs<cplx, cplx>();
+  if (e == cudaSuccess) e = set_smem_attrs<double, double>();
+  if (e == cudaSuccess) e = set_smem_attrs<cplxf, cplx>();
+  if (e == cudaSuccess) e = set_smem_attrs<float, double>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(server_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kWarpBytes * kWarpsPerBlock);
+  return e;
 }
 
 cudaError_t launch_prep(const double* A, int n, int is_real, double* At, double* diag,
@@ -1144,13 +1327,14 @@ cudaError_t launch_prep_batch(const double* const* srcs, const Job* jobs, int nj
   return cudaGetLastError();
 }
 
-cudaError_t launch_subsets(const KernelArgs& a, int is_real, int grid, cudaStream_t st) {
-  const int smem = a.warp_bytes * kWarpsPerBlock;
-  if (is_real)
-    subset_kernel<double><<<grid, 32 * kWarpsPerBlock, smem, st>>>(a);
-  else
-    subset_kernel<cplx><<<grid, 32 * kWarpsPerBlock, smem, st>>>(a);
-  return cudaGetLastError();
+cudaError_t launch_subsets(const KernelArgs& a, int kind, int wpb, int grid, cudaStream_t st) {
+  switch (kind) {
+    case kKindC128: return launch_kind<cplx, cplx>(a, wpb, grid, st);
+    case kKindF64: return launch_kind<double, double>(a, wpb, grid, st);
+    case kKindC64: return launch_kind<cplxf, cplx>(a, wpb, grid, st);
+    case kKindF32: return launch_kind<float, double>(a, wpb, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_server(const ServerArgs& a, int grid, cudaStream_t st) {

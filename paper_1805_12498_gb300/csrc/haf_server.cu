@@ -213,7 +213,7 @@ bool admit_one(haf_server* s) {
   if (s->pending.empty() || s->free_slots.empty()) return false;
   JobRec& j = *s->jobs[s->pending.front()];
   Plan p;
-  if (build_plan({server_spec(s, j.n, j.loops)}, s->sms * kWarpsPerBlock, &p) != HAF_OK) {
+  if (build_plan({server_spec(s, j.n, j.loops)}, s->sms, PlanCfg(), &p) != HAF_OK) {
     s->fatal = HAF_EINVAL;
     s->fatal_msg = "server: planning failed";
     return false;
@@ -514,7 +514,7 @@ int haf_server_submit(haf_server* s, int kind, const double* A, int64_t n, uint6
     if (np != ni) j->A[((size_t)ni * np + ni) * 2] = 1.0;
     // a job larger than the whole arena could never be admitted
     Plan p;
-    if (build_plan({server_spec(s, np, kind)}, s->sms * kWarpsPerBlock, &p) != HAF_OK)
+    if (build_plan({server_spec(s, np, kind)}, s->sms, PlanCfg(), &p) != HAF_OK)
       return sfail(HAF_EINVAL, "haf_server_submit: cannot plan this size");
     if (job_bytes(np, p.chunks.size()) > s->alloc.total)
       return sfail(HAF_ENOMEM, "haf_server_submit: job exceeds the server's device memory");

@@ -24,7 +24,10 @@ def _declared_functions():
 def test_header_declares_entry_points():
     names = _declared_functions()
     for must in ("haf_c128", "lhaf_c128", "haf_f64", "lhaf_f64", "haf_c128_batched",
-                 "lhaf_c128_batched", "haf_launch", "haf_workspace_bytes", "haf_terms_c128"):
+                 "lhaf_c128_batched", "haf_launch", "haf_workspace_bytes", "haf_terms_c128",
+                 "haf_eval", "haf_batched", "haf_terms", "haf_tune", "haf_tune_set", "haf_batched_tune",
+                 "haf_server_create", "haf_server_submit", "haf_server_poll", "haf_server_destroy",
+                 "haf_part", "haf_combine", "haf_launch_noalloc"):
         assert must in names
 
 
@@ -52,3 +55,24 @@ def test_bad_arguments_fail_without_gpu_work():
     assert L.haf_c128(None, 1000, out, None) == _native.HAF_EINVAL
     assert L.haf_launch(None, 5, 0, None, None, 0, None) == _native.HAF_EINVAL
     assert b"n must be even" in L.haf_last_error()
+    A = (ctypes.c_double * 32)()
+    assert L.haf_eval(A, 4, 1 << 7, out, None) == _native.HAF_EINVAL
+    assert b"unknown flags" in L.haf_last_error()
+    assert L.haf_tune_set(16, 0, 5, 8) == _native.HAF_EINVAL
+    assert L.haf_tune_set(16, 0, 8, 0) == _native.HAF_EINVAL
+    assert L.haf_tune_set(15, 0, 8, 8) == _native.HAF_EINVAL
+    r = _native.TuneResult()
+    assert L.haf_tune(16, 0, 0, ctypes.byref(r)) == _native.HAF_EINVAL
+    assert L.haf_tune(16, 1 << 7, 1, ctypes.byref(r)) == _native.HAF_EINVAL
+
+
+def test_precision_limits_match_the_header():
+    """The Python constants of the FP32 mode are the header's."""
+    import paper_1805_12498_gb300 as hg
+    src = open(os.path.join(ROOT, "include", "hafnian_gb300.h")).read()
+    max_n = int(re.search(r"#define HAF_FP32_MAX_N (\d+)", src).group(1))
+    tol = float(re.search(r"#define HAF_FP32_REL_TOL ([0-9.e+-]+)", src).group(1))
+    assert hg.HAF_FP32_MAX_N == max_n and hg.HAF_FP32_REL_TOL == tol
+    assert int(re.search(r"#define HAF_FLAG_FP32 \(1u << (\d+)\)", src).group(1)) == 2
+    with pytest.raises(ValueError):
+        hg._flags(precision="fp16")
