@@ -36,7 +36,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "subset-terms/s (haf, n=48, complex128)"
+def metric_name(n: int) -> str:
+    return f"subset-terms/s (haf, n={n}, complex128)"
 UNIT = "subset-terms/s"
 
 
@@ -265,7 +266,7 @@ def run_reference(args):
         b = cpu_baseline(args.n, args.seed, budget_s=max(5.0, 60.0 / max(1, args.steps)))
         vals.append(b["value"])
     value = statistics.mean(vals) if vals else base["value"]
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric_name(args.n), "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f128 (binary128, CPU oracle)", "data": "synthetic",
             "config": {"workload": f"haf of one seeded complex Gaussian symmetric {args.n}x{args.n} matrix "
@@ -374,7 +375,7 @@ def main():
     achieved = alg_flops(n) / (ms_step * 1e-3) / 1e12
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": metric_name(n), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 (complex128, double-double subset sum)", "data": "synthetic",
             "config": {"workload": f"haf of one seeded complex Gaussian symmetric {n}x{n} matrix per GPU "
