@@ -188,6 +188,29 @@ def precision_leg(seed: int, value48=None):
             "stated_tol_over_abs_sum": hg.HAF_FP32_REL_TOL, "rows": rows}
 
 
+def lowrank_leg(seed: int):
+    """Low-rank hafnian (App. C expansion) at n = 56 for ranks 4, 6, 8:
+    seconds per hafnian and monomials per second (the expansion processes
+    C(k+r-1, r-1) monomials at each degree k = 1..n)."""
+    import math
+
+    import paper_1805_12498_gb300 as hg
+    from paper_1805_12498_gb300 import inputs
+
+    rows = []
+    for n, r in ((56, 4), (56, 6), (56, 8)):
+        g = inputs.rng(seed + 100 * r + n)
+        G = (g.normal(size=(n, r)) + 1j * g.normal(size=(n, r))) / np.sqrt(2 * r)
+        hg.haf_lowrank(G)
+        t = time.perf_counter()
+        a = hg.haf_lowrank(G)
+        dt = time.perf_counter() - t
+        mono = sum(math.comb(k + r - 1, r - 1) for k in range(1, n + 1))
+        rows.append({"n": n, "r": r, "s": dt, "monomials_per_s": mono / dt, "abs_sum": a.abs_sum})
+    return {"workload": "haf(G G^T), G complex Gaussian n x r, App. C expansion on the GPU (host clock, "
+                        "synchronous calls)", "rows": rows}
+
+
 def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
     """Serving (config 4 shape, scaled): haf/lhaf requests (50/50) on GBS
     submatrices, n even in [8, n_max] with P(n) proportional to 2^(-n/8),
@@ -248,10 +271,17 @@ def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
             k += 1
         thr.join()
         wall = time.perf_counter() - t0
+    # the same requests, one synchronous single-matrix call each (the plain
+    # one-launch-per-hafnian form) on the same GPU
+    t = time.perf_counter()
+    for M, loops in reqs:
+        hg.haf_info(M, loops)
+    single = requests / (time.perf_counter() - t)
     lat = np.array(lat) * 1e3
     return {"workload": f"{requests} requests, haf/lhaf 50/50, GBS submatrices of a 32-mode kernel (r=0.88), "
                         f"n even in [8,{n_max}], P(n) ~ 2^(-n/8), Poisson arrivals at {load:g} x capacity",
             "capacity_req_per_s": capacity, "offered_req_per_s": rate, "throughput_req_per_s": requests / wall,
+            "one_launch_per_request_req_per_s": single, "capacity_vs_one_launch": capacity / single,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max())}
 
@@ -399,6 +429,7 @@ def main():
         if args.serve_requests > 0:
             line["serving"] = serving_leg(args.serve_requests, args.serve_nmax, args.seed)
         if not args.no_precision and world == 1:
+            line["lowrank"] = lowrank_leg(args.seed)
             line["precision"] = precision_leg(args.seed, (complex(res[0] + res[2], res[1] + res[3]), float(res[4]),
                                                           ms_step * 1e-3))
         if not args.no_cpu_baseline:

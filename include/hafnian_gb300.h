@@ -204,6 +204,27 @@ int haf_terms(const double* A, int64_t n, uint32_t flags, const uint64_t* masks,
               double* terms);
 
 /* ------------------------------------------------------------------------
+ * Low-rank hafnian (App. C): haf(G G^T) for G with n rows and r columns
+ * (complex128, row-major n x r, owned by the caller), in time
+ * ~ C(n+r-1, r-1) * r^2 instead of 2^{n/2}.  The coefficients lambda_e of
+ * q(x) = prod_i sum_j g_ij x_j (eq. q) are expanded row by row on the GPU
+ * and combined as sum over even e of lambda_e prod_j (e_j - 1)!!.  Only the
+ * entries of G G^T above the diagonal matter (App. C: haf(A) = haf(A + L)),
+ * so any G with G G^T = A + L (L lower triangular) gives haf(A).
+ *   out  : 2 doubles (re, im); info (may be NULL): abs_sum is the same
+ *          expansion with |g_ij| (a bound on every summand; the absolute
+ *          error is a small multiple of 1e-16 n * abs_sum), subsets = number
+ *          of monomials of degree n, C(n+r-1, r-1).
+ * n = 0 gives 1, odd n gives 0.  HAF_EINVAL unless 0 <= n <=
+ * HAF_LOWRANK_MAX_N and 1 <= r <= HAF_LOWRANK_MAX_R; HAF_ENOMEM if the two
+ * degree-n coefficient arrays (48 bytes per monomial in all) do not fit the
+ * free device memory.  Synchronous; uses the current device.
+ * ---------------------------------------------------------------------- */
+#define HAF_LOWRANK_MAX_N 128
+#define HAF_LOWRANK_MAX_R 16
+int haf_lowrank_c128(const double* G, int64_t n, int64_t r, double* out, haf_info* info);
+
+/* ------------------------------------------------------------------------
  * Autotuner (no counterpart in the paper).  The launch shape of a plan is
  * the number of warps per CTA (4, 8 or 16: the shared-memory slice of each
  * warp, hence the lanes per subset and the subsets per CTA, follow from it)

@@ -25,7 +25,7 @@ from ._native import HAF_FLAG_FP32, HAF_FLAG_LOOPS, HAF_FLAG_REAL, HAF_MAX_N, Ha
 
 __all__ = ["haf", "lhaf", "haf_info", "haf_batched", "haf_terms", "workspace_bytes",
            "haf_launch", "haf_part", "part_subsets", "combine", "Server", "fp64_peak", "tune",
-           "tune_set", "batched_tune", "HafError", "HAF_MAX_N", "HAF_FP32_MAX_N", "HAF_FP32_REL_TOL"]
+           "tune_set", "batched_tune", "haf_lowrank", "HafError", "HAF_MAX_N", "HAF_FP32_MAX_N", "HAF_FP32_REL_TOL"]
 
 # FP32-bulk mode: offered for n <= HAF_FP32_MAX_N (include/hafnian_gb300.h)
 HAF_FP32_MAX_N = 56
@@ -223,6 +223,22 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def haf_lowrank(G) -> Info:
+    """haf(G G^T) for an n x r matrix G by the App. C expansion (rank-r
+    inputs; polynomial in n for fixed r).  Only G G^T above the diagonal
+    matters, so any G with G G^T = A + (lower triangular) gives haf(A)."""
+    G = np.asarray(G)
+    if G.ndim != 2:
+        raise ValueError("G must be an n x r matrix")
+    G = np.ascontiguousarray(G, dtype=np.complex128)
+    out = np.zeros(2)
+    info = _native.HafInfo()
+    _native.check(_native.lib().haf_lowrank_c128(G.ctypes.data_as(_native._DP), G.shape[0], G.shape[1],
+                                                 out.ctypes.data_as(_native._DP), ctypes.byref(info)))
+    return Info(complex(out[0], out[1]), info.abs_sum, complex(info.value_lo[0], info.value_lo[1]), info.subsets,
+                info.seconds, info.launches)
 
 
 def tune(n: int, loops: bool = False, real: bool = False, precision: str = "fp64", reps: int = 1) -> dict:

@@ -90,6 +90,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         L.haf_terms_c128.restype = ctypes.c_int
         L.haf_terms.argtypes = [_DP, ctypes.c_int64, ctypes.c_uint32, _U64P, ctypes.c_int64, _DP]
         L.haf_terms.restype = ctypes.c_int
+        L.haf_lowrank_c128.argtypes = [_DP, ctypes.c_int64, ctypes.c_int64, _DP, ctypes.POINTER(HafInfo)]
+        L.haf_lowrank_c128.restype = ctypes.c_int
         L.haf_eval.argtypes = [_DP, ctypes.c_int64, ctypes.c_uint32, _DP, ctypes.POINTER(HafInfo)]
         L.haf_eval.restype = ctypes.c_int
         L.haf_batched.argtypes = [ctypes.POINTER(_DP), _I64P, ctypes.c_int64, ctypes.c_uint32, _DP,

@@ -2,7 +2,7 @@
 
     python -m paper_1805_12498_gb300.build
 
-Two translation units are compiled in parallel with nvcc and linked into a
+The translation units are compiled in parallel with nvcc and linked into a
 shared library that exports the C ABI of include/hafnian_gb300.h.  No
 torch headers are involved: the library depends on the CUDA runtime only.
 """
@@ -19,7 +19,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhafnian_gb300.so")
-SOURCES = ["haf_kernels.cu", "haf_capi.cu", "haf_server.cu"]
+SOURCES = ["haf_kernels.cu", "haf_capi.cu", "haf_server.cu", "haf_lowrank.cu"]
 HEADERS = ["haf_internal.h", os.path.join("..", "..", "include", "hafnian_gb300.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

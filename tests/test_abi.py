@@ -27,7 +27,7 @@ def test_header_declares_entry_points():
                  "lhaf_c128_batched", "haf_launch", "haf_workspace_bytes", "haf_terms_c128",
                  "haf_eval", "haf_batched", "haf_terms", "haf_tune", "haf_tune_set", "haf_batched_tune",
                  "haf_server_create", "haf_server_submit", "haf_server_poll", "haf_server_destroy",
-                 "haf_part", "haf_combine", "haf_launch_noalloc"):
+                 "haf_part", "haf_combine", "haf_launch_noalloc", "haf_lowrank_c128"):
         assert must in names
 
 
@@ -63,6 +63,9 @@ def test_bad_arguments_fail_without_gpu_work():
     assert L.haf_tune_set(15, 0, 8, 8) == _native.HAF_EINVAL
     r = _native.TuneResult()
     assert L.haf_tune(16, 0, 0, ctypes.byref(r)) == _native.HAF_EINVAL
+    assert L.haf_lowrank_c128(None, 4, 2, out, None) == _native.HAF_EINVAL
+    assert L.haf_lowrank_c128(A, 4, 0, out, None) == _native.HAF_EINVAL
+    assert L.haf_lowrank_c128(A, 4, 17, out, None) == _native.HAF_EINVAL
     assert L.haf_tune(16, 1 << 7, 1, ctypes.byref(r)) == _native.HAF_EINVAL
 
 

@@ -156,6 +156,27 @@ def test_all_ones_large(n):
     assert _close(got.value, want, got.abs_sum)
 
 
+def test_maximum_size_exact_values():
+    """HAF_MAX_N = 56: haf(J_56) = 55!! and lhaf(J_52) = T(52) (real path,
+    the size the library is specified up to; about a minute of GPU time)."""
+    got = hg.haf_info(np.ones((56, 56)), real=True)
+    assert _close(got.value, oracle.double_factorial(55), got.abs_sum)
+    got = hg.haf_info(np.ones((52, 52)), loops=True, real=True)
+    assert _close(got.value, oracle.telephone(52), got.abs_sum)
+
+
+@pytest.mark.parametrize("loops", [False, True])
+def test_terms_at_maximum_size(loops):
+    """Sampled summands of a complex Gaussian 56 x 56 matrix (tiles up to
+    56 x 56, the largest shared-memory plan) against the oracle."""
+    A = inputs.complex_gaussian_symmetric(56, 5656)
+    masks = np.concatenate([inputs.random_masks(28, 24, seed=56),
+                            np.array([(1 << 28) - 1, (1 << 28) - 2, 1], dtype=np.uint64)])
+    got = hg.haf_terms(A, masks, loops)
+    want = oracle.terms(A, loops, masks)
+    assert np.all(np.abs(got - want) <= 1e-9 * np.abs(want)), np.max(np.abs(got - want) / np.abs(want))
+
+
 def test_block_diagonal_factorises():
     A = inputs.complex_gaussian_symmetric(10, 61)
     C = inputs.complex_gaussian_symmetric(12, 62)
