@@ -142,10 +142,16 @@ def batched_leg(count: int, seed: int, reps: int = 3):
     t_s = time.perf_counter() - t
     worst = max(abs(v - s.value) / max(s.abs_sum, 1e-300) for v, s in zip(vals, singles))
     subsets = sum(2 ** (nn // 2) for nn in sizes)
+    flops = sum(alg_flops(nn) for nn in sizes)
+    peak, _ = hg.fp64_peak()
     return {"workload": f"{count} GBS submatrices (32 modes, r=0.88, n uniform on even 8..32), complex128",
             "haf_per_s": count / t_b, "subset_terms_per_s": subsets / t_b, "s_per_batch": t_b,
             "one_launch_per_haf_per_s": count / t_s, "speedup_vs_one_launch_per_haf": t_s / t_b,
-            "max_abs_diff_over_abs_sum_vs_single": worst, "timing": "host clock, synchronous calls"}
+            "max_abs_diff_over_abs_sum_vs_single": worst, "timing": "host clock, synchronous calls",
+            "roofline": {"bound": "alu", "achieved": flops / t_b / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / t_b / 1e12 / peak,
+                         "note": "(44/3) 2^h h^2 (h+3) flops summed over the batch / host-clock batch time "
+                                 "(includes the H2D/D2H copies of the graph); peak = DFMA probe (of measured)"}}
 
 
 def precision_leg(seed: int, value48=None):
@@ -206,9 +212,26 @@ def lowrank_leg(seed: int):
         a = hg.haf_lowrank(G)
         dt = time.perf_counter() - t
         mono = sum(math.comb(k + r - 1, r - 1) for k in range(1, n + 1))
-        rows.append({"n": n, "r": r, "s": dt, "monomials_per_s": mono / dt, "abs_sum": a.abs_sum})
+        # minimal traffic: every degree-k array (24 B per monomial: value + abs) written once, read once
+        traffic = 2 * 24 * mono
+        rows.append({"n": n, "r": r, "s": dt, "monomials_per_s": mono / dt, "abs_sum": a.abs_sum,
+                     "roofline": {"bound": "hbm", "achieved": traffic / dt / 1e9, "peak": hbm_peak_gbs(),
+                                  "unit": "GB/s", "frac": traffic / dt / 1e9 / hbm_peak_gbs(),
+                                  "note": "algorithmic bytes = 48 B per monomial update (its degree array "
+                                          "written once and read once); host-clock time; peak = "
+                                          "MEASURED_PEAKS.json hbm_gbs (of measured)"}})
     return {"workload": "haf(G G^T), G complex Gaussian n x r, App. C expansion on the GPU (host clock, "
                         "synchronous calls)", "rows": rows}
+
+
+def hbm_peak_gbs() -> float:
+    """Measured HBM copy bandwidth of this machine's GB300 (MEASURED_PEAKS.json),
+    else the recipe's fallback figure."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
 
 
 def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
