@@ -16,7 +16,9 @@
 // sum_t C(c_t, t+1)), so the state is a dense array in HBM and the rank of
 // e - u_j follows from the bars of e by lowering the bars t >= j by one.
 // One launch per row streams the degree-k array into the degree-(k+1)
-// array (a gather-bound kernel: each entry reads at most r predecessors).
+// array, one entry per thread and grid-stride step (consecutive lanes take
+// consecutive ranks, so the writes coalesce and the predecessor reads of a
+// warp mostly fall in a few lines).
 // The same recurrence on |g_ij| gives, at the end, abs_sum =
 // sum_e Lambda_e prod (e_j - 1)!!, the scale of the rounding error (every
 // summand's magnitude bound), reported like the subset path's sum |f(Z)|.
@@ -49,18 +51,28 @@ __device__ __forceinline__ uint64_t bnm(const uint64_t* b, int R, int a, int c) 
 }
 
 // Bars of the composition with rank `idx` of degree k into r parts:
-// c[0] < ... < c[r-2] in [0, k+r-2], rank = sum_t C(c[t], t+1).
+// c[0] < ... < c[r-2] in [0, k+r-2], rank = sum_t C(c[t], t+1).  Each bar
+// is the largest v with C(v, t+1) <= the remaining rank (binary search).
 __device__ __forceinline__ void unrank_bars(uint64_t idx, int k, int r, const uint64_t* b, int R, int* c) {
   int hi = k + r - 2;
   for (int t = r - 2; t >= 0; --t) {
-    int v = hi;
-    while (v > t && bnm(b, R, v, t + 1) > idx) --v;
-    c[t] = v;
-    idx -= bnm(b, R, v, t + 1);
-    hi = v - 1;
+    int lo = t;  // C(t, t+1) = 0 <= idx always
+    int top = hi;
+    while (lo < top) {
+      const int mid = (lo + top + 1) >> 1;
+      if (bnm(b, R, mid, t + 1) <= idx) lo = mid;
+      else top = mid - 1;
+    }
+    c[t] = lo;
+    idx -= bnm(b, R, lo, t + 1);
+    hi = lo - 1;
   }
 }
 
+// One entry per thread and grid-stride step, so consecutive lanes write
+// (and mostly read) consecutive ranks.  The predecessor ranks follow from
+// prefix sums of C(c_t, t+1) and suffix sums of C(c_t - 1, t+1):
+//   rank(e - u_j) = sum_{t<j} C(c_t, t+1) + sum_{t>=j} C(c_t - 1, t+1).
 __global__ void lowrank_step(const zc* __restrict__ old, const double* __restrict__ old_abs, zc* __restrict__ nw,
                              double* __restrict__ nw_abs, const zc* __restrict__ grow, int k, int r,
                              const uint64_t* __restrict__ binom, int R, uint64_t count) {
@@ -76,22 +88,27 @@ __global__ void lowrank_step(const zc* __restrict__ old, const double* __restric
   }
   for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < count;
        idx += (uint64_t)gridDim.x * blockDim.x) {
-    int c[kLowRankMaxR];
+    int c[kLowRankMaxR + 1];
     unrank_bars(idx, k, r, sb, R, c);
+    c[r - 1] = k + r - 1;  // virtual top bar
+    // suffix sums of C(c_t - 1, t+1), t = j..r-2
+    uint64_t suf[kLowRankMaxR + 1];
+    suf[r - 1] = 0;
+    for (int t = r - 2; t >= 0; --t) suf[t] = suf[t + 1] + bnm(sb, R, c[t] - 1, t + 1);
     double ar = 0.0, ai = 0.0, aa = 0.0;
+    uint64_t pre = 0;  // sum_{t<j} C(c_t, t+1)
+    int cp = -1;
     for (int j = 0; j < r; ++j) {
-      // e_j = c[j] - c[j-1] - 1 (c[-1] = -1, c[r-1] = k + r - 1)
-      const int cj = (j < r - 1) ? c[j] : k + r - 1;
-      const int cp = (j > 0) ? c[j - 1] : -1;
-      if (cj - cp - 1 < 1) continue;
-      uint64_t o = 0;  // rank of e - u_j at degree k-1: bars t >= j move down by one
-      for (int t = 0; t < r - 1; ++t) o += bnm(sb, R, c[t] - (t >= j ? 1 : 0), t + 1);
-      const zc v = old[o];
-      ar = fma(g[j].re, v.re, ar);
-      ar = fma(-g[j].im, v.im, ar);
-      ai = fma(g[j].re, v.im, ai);
-      ai = fma(g[j].im, v.re, ai);
-      aa = fma(ga[j], old_abs[o], aa);
+      const int cj = c[j];
+      if (cj - cp - 1 >= 1) {  // e_j >= 1
+        const uint64_t o = pre + suf[j];
+        const zc v = old[o];
+        ar = fma(g[j].re, v.re, fma(-g[j].im, v.im, ar));
+        ai = fma(g[j].re, v.im, fma(g[j].im, v.re, ai));
+        aa = fma(ga[j], old_abs[o], aa);
+      }
+      if (j < r - 1) pre += bnm(sb, R, cj, j + 1);
+      cp = cj;
     }
     nw[idx] = zc{ar, ai};
     nw_abs[idx] = aa;
@@ -112,37 +129,41 @@ __device__ __forceinline__ void dd_add_lr(double& hi, double& lo, double xh, dou
 }
 
 // Fixed-order reduction of lambda_e prod (e_j - 1)!! over the even
-// compositions of degree n: thread t of the grid takes the contiguous range
-// [t * per, (t + 1) * per), blocks combine in a fixed tree, and block
-// partials go to `part` (5 doubles each: re_hi, re_lo, im_hi, im_lo, abs).
+// compositions of degree n: thread t of the grid (T threads, T fixed) takes
+// the contiguous ranks [t * per, (t + 1) * per); blocks combine in a fixed
+// tree and block partials go to `part` (re_hi, re_lo, im_hi, im_lo, abs).
 __global__ void lowrank_even_sum(const zc* __restrict__ lam, const double* __restrict__ lam_abs, int n, int r,
                                  const uint64_t* __restrict__ binom, int R, const double* __restrict__ dfact,
-                                 uint64_t count, uint64_t per, double* __restrict__ part) {
+                                 uint64_t count, double* __restrict__ part) {
   extern __shared__ uint64_t sb[];
   const int tab = (n + r + 1) * (R + 1);
   for (int i = threadIdx.x; i < tab; i += blockDim.x) sb[i] = binom[i];
   __syncthreads();
   __shared__ double red[5][kLrThreads];
-  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  const uint64_t lo = t * per, hi = min(count, lo + per);
   double rh = 0, rl = 0, ih = 0, il = 0, ab = 0;
-  for (uint64_t idx = lo; idx < hi; ++idx) {
-    int c[kLowRankMaxR];
-    unrank_bars(idx, n, r, sb, R, c);
-    double w = 1.0;
-    bool even = true;
-    for (int j = 0; j < r && even; ++j) {
-      const int cj = (j < r - 1) ? c[j] : n + r - 1;
-      const int cp = (j > 0) ? c[j - 1] : -1;
-      const int e = cj - cp - 1;
-      if (e & 1) even = false;
-      else w *= dfact[e];
-    }
-    if (!even) continue;
+  auto add = [&](uint64_t idx, double w) {
     const zc v = lam[idx];
     dd_add_lr(rh, rl, v.re * w, fma(v.re, w, -(v.re * w)));
     dd_add_lr(ih, il, v.im * w, fma(v.im, w, -(v.im * w)));
     ab += lam_abs[idx] * w;
+  };
+  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t per = (count + T - 1) / T;
+  const uint64_t lo = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * per, hi = min(count, lo + per);
+  for (uint64_t idx = lo; idx < hi; ++idx) {
+    int c[kLowRankMaxR + 1];
+    unrank_bars(idx, n, r, sb, R, c);
+    c[r - 1] = n + r - 1;
+    double w = 1.0;
+    bool even = true;
+    int cp = -1;
+    for (int j = 0; j < r && even; ++j) {
+      const int e = c[j] - cp - 1;
+      if (e & 1) even = false;
+      else w *= dfact[e];
+      cp = c[j];
+    }
+    if (even) add(idx, w);
   }
   red[0][threadIdx.x] = rh;
   red[1][threadIdx.x] = rl;
@@ -233,8 +254,7 @@ extern "C" int haf_lowrank_c128(const double* G, int64_t n64, int64_t r64, doubl
   std::vector<double> df(n + 1, 1.0);
   for (int x = 2; x <= n; ++x) df[x] = df[x - 2] * (double)(x - 1);  // df[x] = (x - 1)!!
   df[0] = 1.0;
-  const int blocks_sum = 1024;
-  const uint64_t per = (maxcount + (uint64_t)blocks_sum * kLrThreads - 1) / ((uint64_t)blocks_sum * kLrThreads);
+  const int blocks_sum = 1024;  // fixed: the reduction order depends on it
   // device buffers
   char* dbuf = nullptr;
   size_t off = 0;
@@ -299,7 +319,7 @@ extern "C" int haf_lowrank_c128(const double* G, int64_t n64, int64_t r64, doubl
   }
   const size_t smem = (size_t)(n + r + 1) * (R + 1) * sizeof(uint64_t);
   lowrank_even_sum<<<blocks_sum, kLrThreads, smem, st>>>(z[cur], za[cur], n, r, bdev, R, (const double*)(dbuf + o_df),
-                                                         maxcount, per, (double*)(dbuf + o_part));
+                                                         maxcount, (double*)(dbuf + o_part));
   lowrank_finish<<<1, 32, 0, st>>>((const double*)(dbuf + o_part), blocks_sum, (double*)(dbuf + o_out));
   launches += 2;
   double res[5];
