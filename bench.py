@@ -295,16 +295,40 @@ def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
         thr.join()
         wall = time.perf_counter() - t0
     # the same requests, one synchronous single-matrix call each (the plain
-    # one-launch-per-hafnian form) on the same GPU
+    # one-launch-per-hafnian form) on the same GPU: its capacity, and its
+    # latency under the same Poisson arrivals with one FIFO worker
     t = time.perf_counter()
     for M, loops in reqs:
         hg.haf_info(M, loops)
     single = requests / (time.perf_counter() - t)
+    import queue
+    q: "queue.Queue" = queue.Queue()
+
+    def arrivals():
+        t_next = time.perf_counter()
+        for (M, loops), gap in zip(reqs, gaps):
+            t_next += gap
+            d = t_next - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            q.put((time.perf_counter(), M, loops))
+
+    thr = th.Thread(target=arrivals)
+    thr.start()
+    fifo = []
+    for _ in range(requests):
+        t_arr, M, loops = q.get()
+        hg.haf_info(M, loops)
+        fifo.append(time.perf_counter() - t_arr)
+    thr.join()
+    fifo = np.array(fifo) * 1e3
     lat = np.array(lat) * 1e3
     return {"workload": f"{requests} requests, haf/lhaf 50/50, GBS submatrices of a 32-mode kernel (r=0.88), "
                         f"n even in [8,{n_max}], P(n) ~ 2^(-n/8), Poisson arrivals at {load:g} x capacity",
             "capacity_req_per_s": capacity, "offered_req_per_s": rate, "throughput_req_per_s": requests / wall,
             "one_launch_per_request_req_per_s": single, "capacity_vs_one_launch": capacity / single,
+            "one_launch_fifo_p50_ms": float(np.percentile(fifo, 50)),
+            "one_launch_fifo_p99_ms": float(np.percentile(fifo, 99)),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max())}
 
