@@ -286,13 +286,6 @@ int upload_plan(const Plan& p, cudaStream_t st, DevPlan* dp) {
   return HAF_OK;
 }
 
-void free_plan(DevPlan* dp) {
-  cudaFree(dp->chunks);
-  cudaFree(dp->order);
-  cudaFree(dp->job_begin);
-  *dp = DevPlan();
-}
-
 // Launch shape for one matrix: the tuned one if haf_tune (or haf_tune_set)
 // recorded one for this (n, kind), else the default: 4 warps per CTA for
 // FP64 (one warp per SM sub-partition saturates the DFMA pipe), 8 for the
