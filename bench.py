@@ -36,6 +36,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) of one launch of the dominant subset kernel at
+# n = 48, from the ncu capture in profiles/subset_kernel_complex_n48_dram.md;
+# re-capture when the kernel changes.
+TRAFFIC_BYTES = {48: 1560320 + 0}
+
+
 def metric_name(n: int) -> str:
     return f"subset-terms/s (haf, n={n}, complex128)"
 UNIT = "subset-terms/s"
@@ -461,11 +467,12 @@ def main():
                        "parallelism": f"independent problems x{world}"},
             "result": {"re": float(res[0] + res[2]), "im": float(res[1] + res[3]), "abs_sum": float(res[4])},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved / peak_tflops, "traffic": None,
+                         "frac": achieved / peak_tflops, "traffic": TRAFFIC_BYTES.get(n),
                          "note": "FP64 pipe; peak = DFMA probe measured in this run (of measured); achieved = "
                                  "(44/3) 2^h h^2 (h+3) flops per step / CUDA-event step time; a step is the "
                                  f"{launches_per_step} launches of one haf_launch (prep, subset-kernel launches, "
-                                 "finalize), the subset kernel >99.9% of it"},
+                                 "finalize), the subset kernel >99.9% of it; traffic = ncu DRAM bytes of "
+                                 "one launch of the dominant subset kernel (profiles/)"},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": n * n * 16,
                     "d2h_bytes_per_step": 5 * 8},
             "gpu_launches": launches_per_step * args.steps,

@@ -114,7 +114,9 @@ def haf_batched(mats, loops: bool = False, with_info: bool = False, precision: s
 
 
 def haf_terms(A, masks, loops: bool = False, precision: str = "fp64") -> np.ndarray:
-    """Unsigned summands f(Z) for the given subset bitmasks (Sec. 3.3)."""
+    """Unsigned summands f(Z) for the given subset bitmasks (Sec. 3.3),
+    computed with the launch shape a whole-matrix call of this size uses."""
+    tuning.ensure_loaded()
     A = _prep(A, False)
     masks = np.ascontiguousarray(np.asarray(masks, dtype=np.uint64))
     out = np.zeros(2 * max(1, masks.size))

@@ -947,7 +947,15 @@ int haf_terms(const double* A, int64_t n64, uint32_t flags, const uint64_t* mask
   for (int64_t i = 0; i < count; ++i)
     if (masks[i] >> h) return fail(HAF_EINVAL, "haf_terms: mask has bits beyond n/2");
   if (count == 0) return HAF_OK;
-  // sort subsets by size; each size becomes chunks of one group-round each
+  // The device and its launch shape for (n, flags): the summands are
+  // computed by the same kernel instantiations, with the same lanes per
+  // subset for each size, as a whole-matrix call of this size.
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device* d;
+  int rc = get_device(&d);
+  if (rc) return rc;
+  const PlanCfg pc = plan_cfg(d, n, loops, 0, prec);
+  // sort subsets by size; each size becomes chunks of four group-rounds
   std::vector<int64_t> perm(count);
   for (int64_t i = 0; i < count; ++i) perm[i] = i;
   std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) {
@@ -957,6 +965,7 @@ int haf_terms(const double* A, int64_t n64, uint32_t flags, const uint64_t* mask
   for (int64_t i = 0; i < count; ++i) sorted[i] = masks[perm[i]];
   Plan p;
   p.job_begin = {0};
+  std::vector<int> seg_of;
   int64_t i = 0;
   while (i < count) {
     const int m = __builtin_popcountll(sorted[i]);
@@ -966,8 +975,12 @@ int haf_terms(const double* A, int64_t n64, uint32_t flags, const uint64_t* mask
       i = e;
       continue;
     }
+    int wpb = pc.wpb;
     SizeCfg cfg;
-    if (!choose_cfg(2 * m, h, kind, kWarpBytes, &cfg)) return fail(HAF_EINVAL, "haf_terms: size too large");
+    while (!choose_cfg(2 * m, h, kind, warp_bytes_for(wpb), &cfg)) {
+      if (wpb == 4) return fail(HAF_EINVAL, "haf_terms: size too large");
+      wpb /= 2;
+    }
     const int S = 32 / cfg.G;
     for (int64_t r = i; r < e; r += 4 * S) {
       Chunk c;
@@ -978,22 +991,27 @@ int haf_terms(const double* A, int64_t n64, uint32_t flags, const uint64_t* mask
       c.G = (uint8_t)cfg.G;
       c.ld = (uint8_t)cfg.ld;
       p.chunks.push_back(c);
+      seg_of.push_back(wpb);
     }
     i = e;
   }
   p.job_begin.push_back((int)p.chunks.size());
-  p.order.resize(p.chunks.size());
-  for (size_t q = 0; q < p.order.size(); ++q) p.order[q] = (int)q;
   p.kind = kind;
-  p.wpb = kWarpsPerBlock;
-  p.warp_bytes = kWarpBytes;
-  p.segs.assign(1, PlanSeg{0, (int)p.chunks.size(), kWarpsPerBlock, kWarpBytes});
+  for (int w : {16, 8, 4}) {
+    PlanSeg sg;
+    sg.begin = (int)p.order.size();
+    for (size_t q = 0; q < p.chunks.size(); ++q)
+      if (seg_of[q] == w) p.order.push_back((int)q);
+    sg.end = (int)p.order.size();
+    if (sg.end == sg.begin) continue;
+    sg.wpb = w;
+    sg.warp_bytes = warp_bytes_for(w);
+    p.segs.push_back(sg);
+  }
+  p.wpb = p.segs.empty() ? kWarpsPerBlock : p.segs[0].wpb;
+  p.warp_bytes = warp_bytes_for(p.wpb);
   std::vector<double> res((size_t)count * 2, 0.0);
   if (!p.chunks.empty()) {
-    std::lock_guard<std::mutex> lk(g_mu);
-    Device* d;
-    int rc = get_device(&d);
-    if (rc) return rc;
     const size_t nn = (size_t)n * n * 16;
     size_t off = 0;
     const size_t a_off = off; off += align256(nn);

@@ -286,6 +286,40 @@ def test_device_launch_matches_host_api():
         assert o[4] == r.abs_sum
 
 
+def _launch_value(A, loops=False):
+    """haf through haf_launch on device memory: the path and launch shape
+    bench.py times."""
+    torch = pytest.importorskip("torch")
+    n = A.shape[0]
+    dev = torch.device("cuda:0")
+    dA = torch.from_numpy(np.ascontiguousarray(A, dtype=np.complex128).view(np.float64)).to(dev)
+    ws = hg.workspace_bytes(n, loops=loops)
+    work = torch.empty(ws // 8 + 64, dtype=torch.float64, device=dev)
+    wptr = (work.data_ptr() + 255) // 256 * 256
+    out = torch.zeros(5, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream()
+    hg.haf_launch(dA.data_ptr(), n, out.data_ptr(), wptr, ws, st.cuda_stream, loops=loops)
+    st.synchronize()
+    o = out.cpu().numpy()
+    return complex(o[0] + o[2], o[1] + o[3]), float(o[4])
+
+
+def test_full_size_in_the_bench_configuration():
+    """n = 48 in the configuration bench.py times (haf_launch, shipped launch
+    shape: an 8-warp launch and a 4-warp launch for the largest tiles):
+    haf(J_48) = 47!!, and a 24 + 24 block-diagonal matrix factorises."""
+    v, scale = _launch_value(np.ones((48, 48), dtype=complex))
+    assert _close(v, oracle.double_factorial(47), scale)
+    A = inputs.complex_gaussian_symmetric(24, 4801)
+    C = inputs.complex_gaussian_symmetric(24, 4802)
+    M = np.zeros((48, 48), dtype=complex)
+    M[:24, :24] = A
+    M[24:, 24:] = C
+    v, scale = _launch_value(M)
+    a, c = hg.haf_info(A), hg.haf_info(C)
+    assert _close(v, a.value * c.value, scale)
+
+
 def test_bitwise_reproducible():
     A = inputs.complex_gaussian_symmetric(28, 55)
     a = hg.haf_info(A)
