@@ -661,18 +661,51 @@ __device__ void loop_moments(const T* __restrict__ tile, int ld, int N, int h,
   }
   u = group_sum_t(u, G);
   if (g == 0) U[1] = u;
+  // Row i of H has N - i + 1 entries (columns i-1..N-1; row 0 has N).  Two
+  // ways to spread the rows over the G lanes, whichever makes the longest
+  // lane shorter for this (N, G):
+  //  - zig-zag: block q of G rows, lane order reversed on odd blocks; the
+  //    warp pays the longest row of each block;
+  //  - pairs: lane g takes the row pairs (p, N-1-p), p = g, g+G, ..., each
+  //    pair walked as one loop of N + 3 entries (N + 2 for p = 0).
+  int zz = 0;
+  for (int q = 0; q * G < N; ++q) zz += N - (q * G > 0 ? q * G - 1 : 0);
+  const bool pairs = ((N / 2 + G - 1) / G) * (N + 3) < zz;
   for (int k = 2; k <= kmax; ++k) {
     __syncwarp();
     T uk = O::zero();
-    // rows in zig-zag order over the lanes (row i has N - i + 1 entries)
-    for (int q = 0; q * G < N; ++q) {
-      const int i = q * G + ((q & 1) ? (G - 1 - g) : g);
-      if (i >= N) continue;
-      const T* row = tile + i * ld;
-      T acc = O::zero();
-      for (int j = (i > 0 ? i - 1 : 0); j < N; ++j) acc = O::fma(row[j], Y0[j], acc);
-      Y1[i] = acc;
-      uk = O::fma(VA[i], acc, uk);
+    if (pairs) {
+      for (int p = g; p < (N >> 1); p += G) {
+        const int i1 = p, i2 = N - 1 - p;
+        const int s1 = p > 0 ? p - 1 : 0, s2 = i2 - 1;
+        const int L1 = N - s1, tot = L1 + (N - s2);
+        const T* row = tile + i1 * ld + s1;
+        const T* y = Y0 + s1;
+        T acc = O::zero(), first = O::zero();
+        for (int t = 0; t < tot; ++t) {
+          if (t == L1) {  // row i1 done: switch to row i2
+            first = acc;
+            acc = O::zero();
+            row = tile + i2 * ld + s2;
+            y = Y0 + s2;
+          }
+          acc = O::fma(*row++, *y++, acc);
+        }
+        Y1[i1] = first;
+        Y1[i2] = acc;
+        uk = O::fma(VA[i1], first, uk);
+        uk = O::fma(VA[i2], acc, uk);
+      }
+    } else {
+      for (int q = 0; q * G < N; ++q) {
+        const int i = q * G + ((q & 1) ? (G - 1 - g) : g);
+        if (i >= N) continue;
+        const T* row = tile + i * ld;
+        T acc = O::zero();
+        for (int j = (i > 0 ? i - 1 : 0); j < N; ++j) acc = O::fma(row[j], Y0[j], acc);
+        Y1[i] = acc;
+        uk = O::fma(VA[i], acc, uk);
+      }
     }
     uk = group_sum_t(uk, G);
     if (g == 0) U[k] = uk;
