@@ -288,7 +288,7 @@ typedef struct haf_server haf_server;
 typedef struct haf_server_cfg {
   int64_t max_jobs;     /* jobs admitted at once (default 256, max 65535)      */
   int64_t max_bytes;    /* device memory for admitted jobs (default 256 MiB)   */
-  int64_t ring_entries; /* chunk descriptor ring entries (default 2^20, >= 2^16) */
+  int64_t ring_entries; /* entries of each of the two descriptor rings (default 2^20, >= 2^16) */
   int64_t idle_us;      /* resident kernel idles out after this (default 20 ms) */
   int64_t chunk_us;     /* target warp time per work chunk (default 4 ms)      */
 } haf_server_cfg;

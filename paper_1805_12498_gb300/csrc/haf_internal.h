@@ -69,11 +69,12 @@ struct SrvJob {
 static_assert(sizeof(SrvJob) % 8 == 0, "SrvJob is moved as 64-bit words");
 
 struct ServerArgs {
-  const Chunk* ring;                  // device: chunk descriptors (written by the host's copies)
-  unsigned long long cap;             // ring entries
-  const unsigned long long* tail;     // device: chunks published so far (host copy, after the entries)
-  unsigned long long* head;           // device: [0] chunks claimed, [1] time of the latest claim,
-                                      // [2..] diagnostic counters
+  const Chunk* ring[2];               // device: chunk descriptors (written by the host's copies);
+                                      // [0] tiles that fit a small slice, [1] larger tiles
+  unsigned long long cap[2];          // ring entries
+  const unsigned long long* tail[2];  // device: chunks published so far (host copy, after the entries)
+  unsigned long long* head;           // device: [kSrvHeadClaim0/1] chunks claimed per ring,
+                                      // [kSrvHeadLast] time of the latest claim, [2..9] diagnostics
   unsigned int* stop;                 // device: nonzero makes every warp leave (set by the host's
                                       // copy at shutdown, or by the first warp that finds the
                                       // kernel idle)
@@ -88,6 +89,16 @@ constexpr int kMaxSmemPerBlock = 232448;  // 227 KiB opt-in on sm_100/sm_103
 constexpr int warp_bytes_for(int wpb) { return (kMaxSmemPerBlock / wpb) / 16 * 16; }
 constexpr int kWarpBytes = warp_bytes_for(kWarpsPerBlock);
 constexpr int kMaxN = 56;
+
+// Server kernel CTA: kSrvSmallWarps warps with the 8-warps-per-CTA slice and
+// one warp with the 4-warps-per-CTA slice (232,448 B in all).
+constexpr int kSrvSmallWarps = 6;
+constexpr int kSrvWarps = kSrvSmallWarps + 1;
+constexpr int kSrvSmallBytes = warp_bytes_for(8);
+constexpr int kSrvBigBytes = warp_bytes_for(4);
+constexpr int kSrvSmemBytes = kSrvSmallWarps * kSrvSmallBytes + kSrvBigBytes;
+static_assert(kSrvSmemBytes <= kMaxSmemPerBlock, "server CTA shared memory");
+constexpr int kSrvHeadClaim0 = 0, kSrvHeadLast = 1, kSrvHeadClaim1 = 10;
 
 // Precision of the bulk steps (gather, Householder, loop moments, La Budde).
 // The power series, f(Z) and the subset sum are FP64 in both modes.

@@ -1018,11 +1018,15 @@ __global__ void __launch_bounds__(32 * WPB, 1) subset_kernel(KernelArgs args) {
 }
 
 // ---------------------------------------------------------------------------
-// Server loop.  Warps claim chunk descriptors from a ring in device memory
-// that the host scheduler appends to, by copy-engine transfers, while the
-// kernel runs: the host copies the new descriptors and then the new
+// Server loop.  Warps claim chunk descriptors from two rings in device
+// memory that the host scheduler appends to, by copy-engine transfers, while
+// the kernel runs: the host copies the new descriptors and then the new
 // published count; a warp reads the count (ld.acquire at gpu scope) and
-// claims the next entry with a compare-and-swap on a device counter.  After
+// claims the next entry with a compare-and-swap on a device counter.  A CTA
+// has kSrvSmallWarps warps with small shared-memory slices and one with a
+// large slice: ring 0 holds chunks whose tiles fit a small slice (planned
+// for 8 warps per CTA), ring 1 the larger tiles, which only the large-slice
+// warp takes (it serves ring 0 too when ring 1 is empty).  After
 // its chunk a warp bumps the job's completed-chunk counter; the warp that
 // completes a job adds the job's chunk partials in chunk order and posts the
 // result and a flag to host memory (release store at system scope).  A warp
@@ -1054,36 +1058,49 @@ __device__ __forceinline__ long long globaltimer() {
 }
 
 template <class T>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) server_kernel(ServerArgs a) {
+__global__ void __launch_bounds__(32 * kSrvWarps, 1) server_kernel(ServerArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* wbase = smem + warp * a.warp_bytes;
-  unsigned long long* const claims = a.head;                                   // [0]
-  volatile long long* const last_claim = reinterpret_cast<volatile long long*>(a.head + 1);
+  // warps 0..kSrvSmallWarps-1 own small slices; the last warp owns the large
+  // one and serves the large-tile ring first, then the small-tile ring
+  const bool big = warp == kSrvSmallWarps;
+  unsigned char* wbase = smem + warp * kSrvSmallBytes;
+  volatile long long* const last_claim = reinterpret_cast<volatile long long*>(a.head + kSrvHeadLast);
   const long long started = globaltimer();
-  unsigned long long t_seen = 0;  // published count this warp has acquired
+  unsigned long long t_seen[2] = {0, 0};  // published counts this warp has acquired, per ring
   for (;;) {
     unsigned long long idx = 0;
     int status = 0;  // 1: claimed an entry, 2: leave
+    int rsel = 0;
     if (lane == 0) {
-      unsigned long long h = atomicAdd(claims, 0ull);
       unsigned int nap = 256;
       for (;;) {
-        if (h < t_seen) {
-          // entries below t_seen are published; take entry h unless another
-          // warp got there first (then retry with the value it left)
-          const unsigned long long prev = atomicCAS(claims, h, h + 1);
-          if (prev == h) {
-            idx = h;
-            status = 1;
-            *last_claim = globaltimer();
-            break;
+        // try the rings this warp serves, in order
+        for (int q = big ? 0 : 1; q < 2 && status == 0; ++q) {
+          const int rg = big ? 1 - q : 0;  // big warp: ring 1, then ring 0
+          unsigned long long* const claims = a.head + (rg ? kSrvHeadClaim1 : kSrvHeadClaim0);
+          unsigned long long h = atomicAdd(claims, 0ull);
+          for (;;) {
+            if (h < t_seen[rg]) {
+              // entries below t_seen are published; take entry h unless another
+              // warp got there first (then retry with the value it left)
+              const unsigned long long prev = atomicCAS(claims, h, h + 1);
+              if (prev == h) {
+                idx = h;
+                rsel = rg;
+                status = 1;
+                *last_claim = globaltimer();
+                break;
+              }
+              h = prev;
+              continue;
+            }
+            const unsigned long long t = ld_acquire_gpu(a.tail[rg]);
+            if (t == t_seen[rg]) break;  // nothing new on this ring
+            t_seen[rg] = t;
           }
-          h = prev;
-          continue;
         }
-        t_seen = ld_acquire_gpu(a.tail);
-        if (h < t_seen) continue;
+        if (status) break;
         atomicAdd(a.head + 2, 1ull);  // diagnostic: idle polls
         if (ld_relaxed_gpu(a.stop) != 0u) {
           status = 2;
@@ -1097,12 +1114,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) server_kernel(ServerAr
         }
         __nanosleep(nap);
         nap = min(nap * 2u, 32768u);
-        h = atomicAdd(claims, 0ull);
       }
     }
     status = __shfl_sync(kFull, status, 0);
     if (status == 2) break;
     idx = __shfl_sync(kFull, idx, 0);
+    rsel = __shfl_sync(kFull, rsel, 0);
     // lane 0 reads the descriptor and the job entry (device memory, through
     // L2) and hands them to the warp
     Chunk ch;
@@ -1110,7 +1127,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) server_kernel(ServerAr
     {
       unsigned long long cw[sizeof(Chunk) / 8], jw[sizeof(SrvJob) / 8];
       if (lane == 0) {
-        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(a.ring + idx % a.cap);
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(a.ring[rsel] + idx % a.cap[rsel]);
 #pragma unroll
         for (int k = 0; k < (int)(sizeof(Chunk) / 8); ++k) cw[k] = __ldcg(src + k);
         const Chunk* cp = reinterpret_cast<const Chunk*>(cw);
@@ -1334,8 +1351,7 @@ cudaError_t configure_kernels() {
   if (e == cudaSuccess) e = set_smem_attrs<cplxf, cplx>();
   if (e == cudaSuccess) e = set_smem_attrs<float, double>();
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(server_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kWarpBytes * kWarpsPerBlock);
+    e = cudaFuncSetAttribute(server_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSrvSmemBytes);
   return e;
 }
 
@@ -1371,7 +1387,7 @@ cudaError_t launch_subsets(const KernelArgs& a, int kind, int wpb, int grid, cud
 }
 
 cudaError_t launch_server(const ServerArgs& a, int grid, cudaStream_t st) {
-  server_kernel<cplx><<<grid, 32 * kWarpsPerBlock, a.warp_bytes * kWarpsPerBlock, st>>>(a);
+  server_kernel<cplx><<<grid, 32 * kSrvWarps, kSrvSmemBytes, st>>>(a);
   return cudaGetLastError();
 }
 

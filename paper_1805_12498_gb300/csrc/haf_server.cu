@@ -5,11 +5,14 @@
 // thread admits them while job slots and device memory allow, prepares each
 // admitted matrix on the host (pair swap X A, upper-triangle symmetrisation,
 // diagonal, Sec. 3.3 eq. matA), copies it into the job's region of a device
-// arena on a copy stream, and then publishes the job's subset chunks into a
-// descriptor ring in device memory that the resident kernel's warps drain
+// arena on a copy stream, and then publishes the job's subset chunks into
+// descriptor rings in device memory that the resident kernel's warps drain
 // (the host stages new descriptors in pinned memory and copies them, then
 // the new published count, on one stream, so a warp that sees the count
-// sees the descriptors below it).  Chunks of
+// sees the descriptors below it).  A job is planned for the kernel's CTA of
+// six small-slice warps and one large-slice warp: chunks whose tiles fit a
+// small slice go to ring 0, which every warp serves; the larger tiles go to
+// ring 1, which the large-slice warp serves first.  Chunks of
 // all admitted jobs are published round robin with a bounded queue depth,
 // so a large-n job is split into chunks that interleave with small jobs
 // that arrive while it runs.  The warp that finishes a job's last chunk
@@ -67,10 +70,10 @@ struct JobRec {
   int slot = -1;
   unsigned int gen = 0;
   size_t off = 0, bytes = 0;  // arena region
-  std::vector<Chunk> chunks;  // publication order
-  size_t next_pub = 0;
-  uint64_t first_pub = UINT64_MAX;
+  std::vector<Chunk> chunks[2];  // per ring (0: small tiles, 1: large), publication order
+  size_t next_pub[2] = {0, 0};
   int64_t subsets = 0;
+  bool all_published() const { return next_pub[0] >= chunks[0].size() && next_pub[1] >= chunks[1].size(); }
   cudaEvent_t uploaded = nullptr;
   double result[5] = {0, 0, 0, 0, 0};
 };
@@ -128,21 +131,26 @@ struct haf_server {
   unsigned int* zeros = nullptr;  // pinned, 256 zero bytes
   double* nan_src = nullptr;      // pinned NaNs (diagnostic fill of partial slots)
   size_t nan_len = 0;
-  unsigned long long* head_dev = nullptr;  // [0] claimed, [1] last claim time, [2..] diagnostics
+  unsigned long long* head_dev = nullptr;  // claims per ring, last claim time, diagnostics (kSrvHead*)
   unsigned int* stop_dev = nullptr;
   double* tables = nullptr;
-  // publication: descriptors and the published count reach the device by copies
-  Chunk* ring_dev = nullptr;
-  Chunk* ring_stage = nullptr;  // pinned, same indexing as ring_dev
-  unsigned long long cap = 0;
-  unsigned long long* tail_dev = nullptr;
+  // publication: descriptors and the published counts reach the device by
+  // copies.  Ring 0 holds chunks whose tiles fit the small warp slices, ring 1
+  // the larger ones (served by the one large-slice warp of each CTA).
+  struct Ring {
+    Chunk* dev = nullptr;
+    Chunk* stage = nullptr;  // pinned, same indexing as dev
+    uint64_t cap = 0;
+    uint64_t published = 0;
+    uint64_t claimed = 0;    // a lower bound, from the read-back
+  } ring[2];
+  unsigned long long* tail_dev = nullptr;  // ring r's count at tail_dev[16 r]
   unsigned long long* tail_src = nullptr;  // pinned rotating sources of the count copies
   unsigned int tail_k = 0;
   unsigned int* flag_src = nullptr;        // pinned: {0, 1} for the stop-flag copies
-  unsigned long long* claimed_h = nullptr; // pinned: read-back of head_dev[0]
+  unsigned long long* claimed_h = nullptr; // pinned: read-back of head_dev[0..kSrvHeadClaim1]
   cudaEvent_t claimed_ev = nullptr;
   bool claimed_pending = false;
-  uint64_t claimed = 0;
   cudaStream_t pub = nullptr, status = nullptr;
   // mapped host memory written by the kernel
   unsigned long long* stats_h = nullptr;
@@ -160,7 +168,6 @@ struct haf_server {
   std::vector<int> free_slots;
   std::vector<unsigned int> slot_gen;
   uint64_t next_ticket = 1;
-  uint64_t published = 0;
   cudaEvent_t kernel_done = nullptr;
   bool kernel_launched = false;
   bool quit = false;
@@ -203,6 +210,15 @@ JobSpec server_spec(const haf_server* s, int n, int loops) {
   return js;
 }
 
+// Server plans: 8 warps per CTA for the tiles that fit the small slices,
+// the rest at 4 (the large-slice warp), matching the server kernel's CTA.
+PlanCfg server_cfg() {
+  PlanCfg c;
+  c.wpb = 8;
+  c.chunks_per_warp = 8;
+  return c;
+}
+
 size_t job_bytes(int n, size_t nchunks) {
   return al256((size_t)n * n * 16) + al256((size_t)n * 16) + al256(nchunks * 5 * sizeof(double)) + 256;
 }
@@ -213,7 +229,7 @@ bool admit_one(haf_server* s) {
   if (s->pending.empty() || s->free_slots.empty()) return false;
   JobRec& j = *s->jobs[s->pending.front()];
   Plan p;
-  if (build_plan({server_spec(s, j.n, j.loops)}, s->sms, PlanCfg(), &p) != HAF_OK) {
+  if (build_plan({server_spec(s, j.n, j.loops)}, s->sms, server_cfg(), &p) != HAF_OK) {
     s->fatal = HAF_EINVAL;
     s->fatal_msg = "server: planning failed";
     return false;
@@ -228,13 +244,19 @@ bool admit_one(haf_server* s) {
   j.off = off;
   j.bytes = bytes;
   j.subsets = p.subsets;
-  j.chunks.resize(p.chunks.size());
-  for (size_t q = 0; q < p.order.size(); ++q) {
-    Chunk c = p.chunks[p.order[q]];
-    c.job = (uint16_t)j.slot;
-    c.tag = (uint16_t)(j.gen & 0xffffu);
-    c.aux = (uint32_t)p.order[q];  // partial slot = index in the job's plan
-    j.chunks[q] = c;
+  for (int r = 0; r < 2; ++r) {
+    j.chunks[r].clear();
+    j.next_pub[r] = 0;
+  }
+  for (const PlanSeg& sg : p.segs) {
+    const int r = sg.wpb == 8 ? 0 : 1;  // 8-warp slices: small ring; 4-warp slices: large ring
+    for (int q = sg.begin; q < sg.end; ++q) {
+      Chunk c = p.chunks[p.order[q]];
+      c.job = (uint16_t)j.slot;
+      c.tag = (uint16_t)(j.gen & 0xffffu);
+      c.aux = (uint32_t)p.order[q];  // partial slot = index in the job's plan
+      j.chunks[r].push_back(c);
+    }
   }
   char* st = s->stage + off;
   const size_t at_b = al256((size_t)j.n * j.n * 16), dg_b = al256((size_t)j.n * 16);
@@ -272,7 +294,9 @@ bool admit_one(haf_server* s) {
 
 void scheduler(haf_server* s) {
   cudaSetDevice(s->dev);
-  const uint64_t depth_target = (uint64_t)s->sms * kWarpsPerBlock;
+  // warps that take chunks from each ring: every warp serves ring 0, the
+  // large-slice warp of each CTA ring 1
+  const uint64_t ring_warps[2] = {(uint64_t)s->sms * kSrvWarps, (uint64_t)s->sms};
   const char* env = std::getenv("HAF_SERVER_LOG");
   const bool log = env && env[0] == '1';
   double last_log = now_s();
@@ -284,11 +308,13 @@ void scheduler(haf_server* s) {
       for (auto& kv : s->jobs) st[kv.second->state]++;
       const bool up = s->kernel_launched && cudaEventQuery(s->kernel_done) == cudaErrorNotReady;
       std::fprintf(stderr,
-                   "[haf_server] pending=%zu uploading=%d ready=%d done=%d published=%llu claimed>=%llu "
+                   "[haf_server] pending=%zu uploading=%d ready=%d done=%d published=%llu/%llu claimed>=%llu/%llu "
                    "kernel=%d launches=%lld free_slots=%zu chunks_done=%llu chunk_ns=%llu idle_polls=%llu "
                    "stale=%llu over=%llu unwritten=%llu\n",
-                   s->pending.size(), st[kUploading], st[kReady], st[kDone], (unsigned long long)s->published,
-                   (unsigned long long)s->claimed, up ? 1 : 0, (long long)s->launches, s->free_slots.size(),
+                   s->pending.size(), st[kUploading], st[kReady], st[kDone],
+                   (unsigned long long)s->ring[0].published, (unsigned long long)s->ring[1].published,
+                   (unsigned long long)s->ring[0].claimed, (unsigned long long)s->ring[1].claimed, up ? 1 : 0,
+                   (long long)s->launches, s->free_slots.size(),
                    (unsigned long long)__atomic_load_n(s->stats_h, __ATOMIC_RELAXED),
                    (unsigned long long)__atomic_load_n(s->stats_h + 1, __ATOMIC_RELAXED),
                    (unsigned long long)__atomic_load_n(s->stats_h + 2, __ATOMIC_RELAXED),
@@ -301,7 +327,7 @@ void scheduler(haf_server* s) {
     // 1. completions
     for (auto& kv : s->jobs) {
       JobRec& j = *kv.second;
-      if (j.state != kReady || j.next_pub < j.chunks.size()) continue;
+      if (j.state != kReady || !j.all_published()) continue;
       if (__atomic_load_n(&s->flags_h[j.slot], __ATOMIC_ACQUIRE) == j.gen) {
         volatile double* r = s->results_h + 5 * j.slot;
         for (int k = 0; k < 5; ++k) j.result[k] = r[k];
@@ -328,74 +354,79 @@ void scheduler(haf_server* s) {
     //    before it claims another, so at most one claimed-but-unread entry
     //    per warp exists, which the margin covers.
     if (s->claimed_pending && cudaEventQuery(s->claimed_ev) == cudaSuccess) {
-      s->claimed = std::max<uint64_t>(s->claimed, *s->claimed_h);
+      s->ring[0].claimed = std::max<uint64_t>(s->ring[0].claimed, s->claimed_h[kSrvHeadClaim0]);
+      s->ring[1].claimed = std::max<uint64_t>(s->ring[1].claimed, s->claimed_h[kSrvHeadClaim1]);
       s->claimed_pending = false;
     }
     if (!s->claimed_pending) {
-      if (cudaMemcpyAsync(s->claimed_h, s->head_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                          s->status) == cudaSuccess &&
+      if (cudaMemcpyAsync(s->claimed_h, s->head_dev, (kSrvHeadClaim1 + 1) * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, s->status) == cudaSuccess &&
           cudaEventRecord(s->claimed_ev, s->status) == cudaSuccess)
         s->claimed_pending = true;
     }
-    const uint64_t claimed = std::min<uint64_t>(s->claimed, s->published);
-    const uint64_t margin = 4ull * (uint64_t)s->sms * kWarpsPerBlock;
-    const uint64_t lim = (claimed > margin ? claimed - margin : 0) + s->cap;
-    bool progress = true;
-    const uint64_t before = s->published;
-    while (progress) {
-      progress = false;
-      for (auto& kv : s->jobs) {
-        JobRec& j = *kv.second;
-        if (j.state != kReady || j.next_pub >= j.chunks.size()) continue;
-        if (s->published - claimed >= depth_target || s->published >= lim) break;
-        const size_t burst = 4;
-        for (size_t q = 0; q < burst && j.next_pub < j.chunks.size() && s->published < lim; ++q) {
-          if (j.first_pub == UINT64_MAX) j.first_pub = s->published;
-          s->ring_stage[s->published % s->cap] = j.chunks[j.next_pub++];
-          ++s->published;
-          progress = true;
+    for (int r = 0; r < 2; ++r) {
+      haf_server::Ring& R = s->ring[r];
+      // queue depth: about one chunk per warp that serves the ring
+      const uint64_t claimed = std::min<uint64_t>(R.claimed, R.published);
+      const uint64_t margin = 4ull * ring_warps[r];
+      const uint64_t lim = (claimed > margin ? claimed - margin : 0) + R.cap;
+      bool progress = true;
+      const uint64_t before = R.published;
+      while (progress) {
+        progress = false;
+        for (auto& kv : s->jobs) {
+          JobRec& j = *kv.second;
+          if (j.state != kReady || j.next_pub[r] >= j.chunks[r].size()) continue;
+          if (R.published - claimed >= ring_warps[r] || R.published >= lim) break;
+          const size_t burst = 4;
+          for (size_t q = 0; q < burst && j.next_pub[r] < j.chunks[r].size() && R.published < lim; ++q) {
+            R.stage[R.published % R.cap] = j.chunks[r][j.next_pub[r]++];
+            ++R.published;
+            progress = true;
+          }
         }
       }
-    }
-    if (s->published != before) {
-      // copy the new entries (one or two contiguous pieces), then the count
-      cudaError_t e = cudaSuccess;
-      uint64_t p0 = before;
-      while (e == cudaSuccess && p0 < s->published) {
-        const uint64_t i0 = p0 % s->cap;
-        const uint64_t len = std::min<uint64_t>(s->published - p0, s->cap - i0);
-        e = cudaMemcpyAsync(s->ring_dev + i0, s->ring_stage + i0, len * sizeof(Chunk), cudaMemcpyHostToDevice,
-                            s->pub);
-        p0 += len;
-      }
-      unsigned long long* src = s->tail_src + (s->tail_k++ & 4095u);
-      *src = s->published;
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->tail_dev, src, sizeof(unsigned long long), cudaMemcpyHostToDevice, s->pub);
-      if (e != cudaSuccess) {
-        s->fatal = HAF_ECUDA;
-        s->fatal_msg = std::string("server publish: ") + cudaGetErrorString(e);
+      if (R.published != before) {
+        // copy the new entries (one or two contiguous pieces), then the count
+        cudaError_t e = cudaSuccess;
+        uint64_t p0 = before;
+        while (e == cudaSuccess && p0 < R.published) {
+          const uint64_t i0 = p0 % R.cap;
+          const uint64_t len = std::min<uint64_t>(R.published - p0, R.cap - i0);
+          e = cudaMemcpyAsync(R.dev + i0, R.stage + i0, len * sizeof(Chunk), cudaMemcpyHostToDevice, s->pub);
+          p0 += len;
+        }
+        unsigned long long* src = s->tail_src + (s->tail_k++ & 4095u);
+        *src = R.published;
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(s->tail_dev + 16 * r, src, sizeof(unsigned long long), cudaMemcpyHostToDevice, s->pub);
+        if (e != cudaSuccess) {
+          s->fatal = HAF_ECUDA;
+          s->fatal_msg = std::string("server publish: ") + cudaGetErrorString(e);
+        }
       }
     }
     // 5. keep the resident kernel running while any admitted job is unfinished
     for (auto& kv : s->jobs)
       if (kv.second->state == kReady || kv.second->state == kUploading) active = true;
-    if (active && s->published > 0) {
+    if (active && s->ring[0].published + s->ring[1].published > 0) {
       bool running = s->kernel_launched && cudaEventQuery(s->kernel_done) == cudaErrorNotReady;
       if (!running) {
         // the previous instance has ended (its warps raised the stop flag
         // together when idle): clear the flag, in stream order, for the new one
         ServerArgs a;
-        a.ring = s->ring_dev;
-        a.cap = s->cap;
-        a.tail = s->tail_dev;
+        for (int r = 0; r < 2; ++r) {
+          a.ring[r] = s->ring[r].dev;
+          a.cap[r] = s->ring[r].cap;
+          a.tail[r] = s->tail_dev + 16 * r;
+        }
         a.head = s->head_dev;
         a.stop = s->stop_dev;
         a.stats = s->stats_d;
         a.jobs = s->jobs_dev;
         a.tables = s->tables;
         a.idle_ns = (long long)s->cfg.idle_us * 1000LL;
-        a.warp_bytes = kWarpBytes;
+        a.warp_bytes = kSrvSmallBytes;
         cudaError_t e = cudaMemcpyAsync(s->stop_dev, s->flag_src, sizeof(unsigned int), cudaMemcpyHostToDevice,
                                         s->comp);
         if (e == cudaSuccess) e = launch_server(a, s->sms, s->comp);
@@ -460,12 +491,14 @@ int haf_server_create(const haf_server_cfg* cfg, haf_server** out) {
   for (int k = 1; k < 128; ++k) tab[128 + k] = 1.0 / k;
   SRV_CUDA(cudaMalloc(&s->tables, 256 * sizeof(double)));
   SRV_CUDA(cudaMemcpy(s->tables, tab.data(), 256 * sizeof(double), cudaMemcpyHostToDevice));
-  s->cap = (unsigned long long)s->cfg.ring_entries;
+  for (int r = 0; r < 2; ++r) s->ring[r].cap = (uint64_t)s->cfg.ring_entries;
   SRV_CUDA(cudaStreamCreateWithFlags(&s->pub, cudaStreamNonBlocking));
   SRV_CUDA(cudaStreamCreateWithFlags(&s->status, cudaStreamNonBlocking));
   SRV_CUDA(cudaEventCreateWithFlags(&s->claimed_ev, cudaEventDisableTiming));
-  SRV_CUDA(cudaMalloc(&s->ring_dev, sizeof(Chunk) * s->cap));
-  SRV_CUDA(cudaMallocHost(&s->ring_stage, sizeof(Chunk) * s->cap));
+  for (int r = 0; r < 2; ++r) {
+    SRV_CUDA(cudaMalloc(&s->ring[r].dev, sizeof(Chunk) * s->ring[r].cap));
+    SRV_CUDA(cudaMallocHost(&s->ring[r].stage, sizeof(Chunk) * s->ring[r].cap));
+  }
   SRV_CUDA(cudaMalloc(&s->tail_dev, 256));
   SRV_CUDA(cudaMemset(s->tail_dev, 0, 256));
   SRV_CUDA(cudaMalloc(&s->stop_dev, 256));
@@ -474,8 +507,8 @@ int haf_server_create(const haf_server_cfg* cfg, haf_server** out) {
   SRV_CUDA(cudaMallocHost(&s->flag_src, 2 * sizeof(unsigned int)));
   s->flag_src[0] = 0u;
   s->flag_src[1] = 1u;
-  SRV_CUDA(cudaMallocHost(&s->claimed_h, sizeof(unsigned long long)));
-  *s->claimed_h = 0;
+  SRV_CUDA(cudaMallocHost(&s->claimed_h, (kSrvHeadClaim1 + 1) * sizeof(unsigned long long)));
+  std::memset(s->claimed_h, 0, (kSrvHeadClaim1 + 1) * sizeof(unsigned long long));
   SRV_CUDA(cudaHostAlloc(&s->stats_h, 256, cudaHostAllocMapped));
   std::memset(s->stats_h, 0, 256);
   SRV_CUDA(cudaHostAlloc(&s->results_h, sizeof(double) * 5 * mj, cudaHostAllocMapped));
@@ -514,7 +547,7 @@ int haf_server_submit(haf_server* s, int kind, const double* A, int64_t n, uint6
     if (np != ni) j->A[((size_t)ni * np + ni) * 2] = 1.0;
     // a job larger than the whole arena could never be admitted
     Plan p;
-    if (build_plan({server_spec(s, np, kind)}, s->sms, PlanCfg(), &p) != HAF_OK)
+    if (build_plan({server_spec(s, np, kind)}, s->sms, server_cfg(), &p) != HAF_OK)
       return sfail(HAF_EINVAL, "haf_server_submit: cannot plan this size");
     if (job_bytes(np, p.chunks.size()) > s->alloc.total)
       return sfail(HAF_ENOMEM, "haf_server_submit: job exceeds the server's device memory");
@@ -585,8 +618,10 @@ int haf_server_destroy(haf_server* s) {
   cudaFree(s->head_dev);
   cudaFree(s->stop_dev);
   cudaFree(s->tables);
-  cudaFree(s->ring_dev);
-  cudaFreeHost(s->ring_stage);
+  for (int r = 0; r < 2; ++r) {
+    cudaFree(s->ring[r].dev);
+    cudaFreeHost(s->ring[r].stage);
+  }
   cudaFree(s->tail_dev);
   cudaFreeHost(s->tail_src);
   cudaFreeHost(s->flag_src);
