@@ -728,8 +728,8 @@ __device__ void loop_moments(const T* __restrict__ tile, int ld, int N, int h,
 // The sum is evaluated "right-looking": once D_r is final, its terms
 //   D_{r+1}[j]   += D_r[j] - alpha_r D_r[j-1]
 //   D_i[t+i-r]   -= H'_{r, i-1} D_r[t]          (i = r+2..N)
-// are added to every later polynomial; the (i, t) pairs of one r are spread
-// evenly over the group's lanes.  D_i[1..min(i,h)] for i < N accumulate in
+// are added to every later polynomial; the (i, t) pairs of one r are dealt
+// round robin over the group's lanes.  D_i[1..min(i,h)] for i < N accumulate in
 // row i of the tile, columns 0..i-1 (free after the reduction: entries
 // below the subdiagonal and, once folded, the subdiagonal); D_N goes to DN.
 // ---------------------------------------------------------------------------
@@ -742,13 +742,22 @@ template <class T>
 __device__ void labudde(T* __restrict__ tile, int ld, int N, int h, T* __restrict__ DN, int g,
                         int G) {
   using O = Ops<T>;
-  // fold the subdiagonal products into the upper triangle
-  for (int b = (g == 0 ? G : g); b < N; b += G) {
-    T rho = tile[b * ld + b - 1];
-    tile[(b - 1) * ld + b] = O::mul(tile[(b - 1) * ld + b], rho);
-    for (int a = b - 2; a >= 0; --a) {
-      rho = O::mul(rho, tile[(a + 1) * ld + a]);
-      tile[a * ld + b] = O::mul(tile[a * ld + b], rho);
+  // Fold the subdiagonal products into the upper triangle, row by row:
+  // H'_{a,b} = H_{a,b} s_{a+1} s_{a+2} ... s_b (s_l = H_{l,l-1}).  Row a has
+  // N-1-a entries, so rows a and N-2-a together have N: each lane takes such
+  // pairs (the middle row alone), which keeps the lanes' work equal.
+  for (int p = g; p < (N >> 1); p += G) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int a = half ? N - 2 - p : p;
+      if (half && a == p) break;  // middle row: once
+      T* row = tile + a * ld;
+      T rho = tile[(a + 1) * ld + a];
+      row[a + 1] = O::mul(row[a + 1], rho);
+      for (int b = a + 2; b < N; ++b) {
+        rho = O::mul(rho, tile[b * ld + b - 1]);
+        row[b] = O::mul(row[b], rho);
+      }
     }
   }
   __syncwarp();
@@ -771,29 +780,25 @@ __device__ void labudde(T* __restrict__ tile, int ld, int N, int h, T* __restric
       *a = O::fnma(alpha, dm, O::add(*a, d));
     }
     // (b) D_i[t+i-r] -= H'_{r,i-1} D_r[t] for rows i = r+2..imax and
-    //     t = 0..min(ra, h-(i-r)).  Lanes form a Gi x Gt grid over (row, t),
-    //     with the split chosen per r to balance rows against coefficients.
+    //     t = 0..min(ra, h-(i-r)).  The (i, t) pairs, row by row, are dealt
+    //     to the lanes round robin (lane g takes pairs g, g+G, ...), so the
+    //     lanes' shares differ by at most one.
     const int ra = min(r, h);
     const int imax = min(N, h + r);
-    const int nrows = imax - (r + 1);
-    if (nrows > 0) {
-      int Gi = 1, best = 1 << 30;
-      for (int gi = 1; gi <= G; gi <<= 1) {
-        const int cost = ((nrows + gi - 1) / gi) * ((ra + 1 + (G / gi) - 1) / (G / gi));
-        if (cost < best) {
-          best = cost;
-          Gi = gi;
-        }
+    {
+      int i = r + 2, t = g;
+      while (i <= imax && t > min(ra, h - (i - r))) {
+        t -= min(ra, h - (i - r)) + 1;
+        ++i;
       }
-      const int Gt = G / Gi;
-      const int gi = g & (Gi - 1), gt = g / Gi;
-      for (int i = r + 2 + gi; i <= imax; i += Gi) {
-        const T hri = Hr[i - 1];
-        const int tmax = min(ra, h - (i - r));
+      while (i <= imax) {
+        const T d = (t == 0) ? O::one() : Dr[t];
         T* a = dslot(tile, ld, N, DN, i, i - r);  // D_i[t + i - r] = a[t]
-        for (int t = gt; t <= tmax; t += Gt) {
-          const T d = (t == 0) ? O::one() : Dr[t];
-          a[t] = O::fnma(hri, d, a[t]);
+        a[t] = O::fnma(Hr[i - 1], d, a[t]);
+        t += G;
+        while (i <= imax && t > min(ra, h - (i - r))) {
+          t -= min(ra, h - (i - r)) + 1;
+          ++i;
         }
       }
     }
