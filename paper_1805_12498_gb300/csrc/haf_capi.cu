@@ -4,11 +4,14 @@
 //
 // Plan.  For a matrix of size n (h = n/2 pairs), subsets of size m = 1..h
 // (the empty subset contributes 0 for h >= 1) are grouped into chunks of
-// consecutive colex ranks.  Each size gets a lane-group width G (1..32
-// lanes per subset, 32/G subsets per warp), the smallest that fits the
-// warp's shared-memory slice, and chunks are ordered largest-work-first so
-// the persistent warps finish together.  Each chunk writes one partial;
-// partials are reduced in chunk order, independent of scheduling.
+// consecutive colex ranks.  A plan has a launch shape (warps per CTA, chunk
+// granularity; tuned per size by haf_tune, else a default).  Each size gets
+// a lane-group width G (1..32 lanes per subset, 32/G subsets per warp), the
+// smallest that fits the warp's shared-memory slice; sizes whose tiles do
+// not fit at the plan's warps per CTA run in a second launch with fewer.
+// Within a launch chunks are ordered largest-work-first so the persistent
+// warps finish together.  Each chunk writes one partial; partials are
+// reduced in chunk order, independent of scheduling.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -82,7 +82,6 @@ struct ServerArgs {
   const SrvJob* jobs;                 // device job table
   const double* tables;
   long long idle_ns;                  // the kernel leaves after this long without a claim
-  int warp_bytes;
 };
 constexpr int kMaxSmemPerBlock = 232448;  // 227 KiB opt-in on sm_100/sm_103
 // Shared memory owned by each warp when a CTA has `wpb` warps.

@@ -26,11 +26,16 @@
 // cycles per SM sub-partition and charges idle lanes in full, so the kernel
 // is organised around lane occupancy of the FP64 pipe: a warp processes
 // S = 32/G subsets of the same size |Z| = m in lock step, G lanes per
-// subset, every tile in the warp's own slice of shared memory.  Persistent
-// warps pull chunks of colex-ordered subsets of one size from a work list
+// subset, every tile in the warp's own slice of shared memory.  A CTA has
+// 4, 8 or 16 warps (a template parameter; the slice per warp shrinks
+// accordingly), one CTA per SM; two warps per sub-partition keep the FP64
+// pipe busier while the other waits on shared memory.  Persistent warps
+// pull chunks of colex-ordered subsets of one size from a work list
 // (largest tiles first).  Each chunk's signed terms are summed in
 // double-double and written to its own slot; a finalize kernel adds the
-// slots in a fixed order, so results do not depend on scheduling.
+// slots in a fixed order, so results do not depend on scheduling.  The same
+// code runs in single precision for the FP32-bulk mode (bulk type cplxf /
+// float, series and sum in FP64).
 #include <cuda_runtime.h>
 #include <stdint.h>
 

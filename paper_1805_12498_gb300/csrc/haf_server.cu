@@ -426,7 +426,6 @@ void scheduler(haf_server* s) {
         a.jobs = s->jobs_dev;
         a.tables = s->tables;
         a.idle_ns = (long long)s->cfg.idle_us * 1000LL;
-        a.warp_bytes = kSrvSmallBytes;
         cudaError_t e = cudaMemcpyAsync(s->stop_dev, s->flag_src, sizeof(unsigned int), cudaMemcpyHostToDevice,
                                         s->comp);
         if (e == cudaSuccess) e = launch_server(a, s->sms, s->comp);
