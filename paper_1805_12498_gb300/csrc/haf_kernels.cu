@@ -595,13 +595,49 @@ __device__ __forceinline__ void range_colsum(const T* tile, int ld, int k1, int 
 //   t_j = sum_{i in K} conj(w_i) A_ij - gamma conj(w_j);
 //   A_ij -= p_i conj(w_j) (all rows) and -= w_i t_j (rows in K),
 // which is A <- (I - w w^H) A (I - w w^H) restricted to the active block.
-// With `loops`, va <- va (I - w w^H) and vb <- (I - w w^H) vb as well.
+// With `loops` the reduction starts from b ("Krylov start"): a first
+// reflector on all N indices maps vb to alpha e_0 and is applied to A from
+// both sides and to va; the later steps act on indices >= 1, so vb stays
+// alpha e_0 while va <- va (I - w w^H) follows every step.  Then
+// H^{k-1} vb is supported on its first k entries (H is Hessenberg), which
+// is what makes the loop moments cheap.
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__ W,
                             T* __restrict__ P, T* __restrict__ TV, T* __restrict__ VA,
                             T* __restrict__ VB, T* __restrict__ X, bool loops, int g, int G) {
   using O = Ops<T>;
+  if (loops) {
+    using R = typename O::R;
+    R sig = R(0);
+    for (int i = 1 + g; i < N; i += G) sig = O::abs2_acc(VB[i], sig);
+    sig = group_sum(sig, G);
+    const T x0 = VB[0];
+    const R s0 = O::abs2(x0);
+    R c;
+    T w0, alpha;
+    O::reflector(x0, s0, s0 + sig, c, w0, alpha);
+    for (int i = 1 + g; i < N; i += G) W[i] = O::scale(VB[i], c);
+    if (g == 0) W[0] = w0;
+    __syncwarp();
+    range_matvec<T>(tile, ld, 0, N, 0, N, g, G, W, P, X);  // p = A w
+    __syncwarp();
+    T gam = O::zero();
+    for (int i = g; i < N; i += G) gam = O::cfma(W[i], P[i], gam);
+    gam = group_sum_t(gam, G);
+    __syncwarp();
+    range_colsum<T>(tile, ld, 0, N, g, G, W, gam, TV, X);  // t_j, every column
+    T aw = O::zero();
+    for (int i = g; i < N; i += G) aw = O::fma(VA[i], W[i], aw);
+    aw = group_sum_t(aw, G);
+    for (int i = g; i < N; i += G) {
+      VA[i] = O::fnma_cb(aw, W[i], VA[i]);
+      VB[i] = (i == 0) ? alpha : O::zero();
+    }
+    __syncwarp();
+    range_update<T, true>(tile, ld, 0, N, 0, N, g, G, W, TV, P);  // every row, both sides
+    __syncwarp();
+  }
   for (int k = 0; k + 2 < N; ++k) {
     const int k1 = k + 1;
     const int i2 = k + 2 + g;  // this lane's rows below the first reflected entry
@@ -627,18 +663,11 @@ __device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__
     gam = group_sum_t(gam, G);
     __syncwarp();
     range_colsum<T>(tile, ld, k1, N, g, G, W, gam, TV, X);  // t_j
-    if (loops) {
-      T aw = O::zero(), wb = O::zero();
-      for (int i = k1 + g; i < N; i += G) {
-        aw = O::fma(VA[i], W[i], aw);
-        wb = O::cfma(W[i], VB[i], wb);
-      }
+    if (loops) {  // va <- va (I - w w^H); vb = alpha e_0 is untouched (w_0 = 0)
+      T aw = O::zero();
+      for (int i = k1 + g; i < N; i += G) aw = O::fma(VA[i], W[i], aw);
       aw = group_sum_t(aw, G);
-      wb = group_sum_t(wb, G);
-      for (int i = k1 + g; i < N; i += G) {
-        VA[i] = O::fnma_cb(aw, W[i], VA[i]);
-        VB[i] = O::fnma(W[i], wb, VB[i]);
-      }
+      for (int i = k1 + g; i < N; i += G) VA[i] = O::fnma_cb(aw, W[i], VA[i]);
     }
     __syncwarp();
     range_update<T, false>(tile, ld, k1, N, 0, k1, g, G, W, TV, P);  // rows above K
@@ -650,8 +679,10 @@ __device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__
 // ---------------------------------------------------------------------------
 // Loop moments u_k = a H^{k-1} b, k = 1..min(h, N), for the loop hafnian
 // (a = v Q, b = Q^H X v^T after the reduction, so u_k = v B^{k-1} X v^T).
-// Y0, Y1: scratch vectors of length N.  Uses the Hessenberg structure of H
-// (row i has entries in columns >= i-1).
+// The reduction started from b, so b = beta e_0 and y_k = H^{k-1} b is
+// supported on entries 0..k-1: step k computes rows 0..k-1 of H y_{k-1}
+// from columns 0..k-2 only (row i from column max(i-1, 0)), about k^2/2
+// multiply-adds instead of N^2/2.  Y0, Y1: scratch vectors of length N.
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ void loop_moments(const T* __restrict__ tile, int ld, int N, int h,
@@ -659,58 +690,22 @@ __device__ void loop_moments(const T* __restrict__ tile, int ld, int N, int h,
                              T* __restrict__ U, int g, int G) {
   using O = Ops<T>;
   const int kmax = min(h, N);
-  T u = O::zero();
-  for (int i = g; i < N; i += G) {
-    Y0[i] = VB[i];
-    u = O::fma(VA[i], VB[i], u);
+  if (g == 0) {
+    Y0[0] = VB[0];
+    U[1] = O::mul(VA[0], VB[0]);
   }
-  u = group_sum_t(u, G);
-  if (g == 0) U[1] = u;
-  // Row i of H has N - i + 1 entries (columns i-1..N-1; row 0 has N).  Two
-  // ways to spread the rows over the G lanes, whichever makes the longest
-  // lane shorter for this (N, G):
-  //  - zig-zag: block q of G rows, lane order reversed on odd blocks; the
-  //    warp pays the longest row of each block;
-  //  - pairs: lane g takes the row pairs (p, N-1-p), p = g, g+G, ..., each
-  //    pair walked as one loop of N + 3 entries (N + 2 for p = 0).
-  int zz = 0;
-  for (int q = 0; q * G < N; ++q) zz += N - (q * G > 0 ? q * G - 1 : 0);
-  const bool pairs = ((N / 2 + G - 1) / G) * (N + 3) < zz;
   for (int k = 2; k <= kmax; ++k) {
     __syncwarp();
     T uk = O::zero();
-    if (pairs) {
-      for (int p = g; p < (N >> 1); p += G) {
-        const int i1 = p, i2 = N - 1 - p;
-        const int s1 = p > 0 ? p - 1 : 0, s2 = i2 - 1;
-        const int L1 = N - s1, tot = L1 + (N - s2);
-        const T* row = tile + i1 * ld + s1;
-        const T* y = Y0 + s1;
-        T acc = O::zero(), first = O::zero();
-        for (int t = 0; t < tot; ++t) {
-          if (t == L1) {  // row i1 done: switch to row i2
-            first = acc;
-            acc = O::zero();
-            row = tile + i2 * ld + s2;
-            y = Y0 + s2;
-          }
-          acc = O::fma(*row++, *y++, acc);
-        }
-        Y1[i1] = first;
-        Y1[i2] = acc;
-        uk = O::fma(VA[i1], first, uk);
-        uk = O::fma(VA[i2], acc, uk);
-      }
-    } else {
-      for (int q = 0; q * G < N; ++q) {
-        const int i = q * G + ((q & 1) ? (G - 1 - g) : g);
-        if (i >= N) continue;
-        const T* row = tile + i * ld;
-        T acc = O::zero();
-        for (int j = (i > 0 ? i - 1 : 0); j < N; ++j) acc = O::fma(row[j], Y0[j], acc);
-        Y1[i] = acc;
-        uk = O::fma(VA[i], acc, uk);
-      }
+    // rows 0..k-1 in zig-zag order over the lanes (row i has k - max(i, 1) entries)
+    for (int q = 0; q * G < k; ++q) {
+      const int i = q * G + ((q & 1) ? (G - 1 - g) : g);
+      if (i >= k) continue;
+      const T* row = tile + i * ld;
+      T acc = O::zero();
+      for (int j = (i > 0 ? i - 1 : 0); j <= k - 2; ++j) acc = O::fma(row[j], Y0[j], acc);
+      Y1[i] = acc;
+      uk = O::fma(VA[i], acc, uk);
     }
     uk = group_sum_t(uk, G);
     if (g == 0) U[k] = uk;
