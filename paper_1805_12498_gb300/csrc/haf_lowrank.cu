@@ -29,6 +29,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -207,6 +209,19 @@ __global__ void lowrank_finish(const double* __restrict__ part, int nblocks, dou
 
 int lfail(int code, const std::string& msg) { return set_error(code, msg); }
 
+// Per-device stream and workspace kept between calls (calls are serialised
+// by the mutex).  Workspaces up to kLrKeepBytes stay allocated, so repeated
+// small expansions pay no cudaMalloc/cudaFree; larger ones are released
+// after their call.
+constexpr size_t kLrKeepBytes = (size_t)256 << 20;
+struct LrDevice {
+  cudaStream_t st = nullptr;
+  char* buf = nullptr;
+  size_t bytes = 0;
+};
+std::mutex g_lr_mu;
+std::map<int, LrDevice> g_lr_dev;
+
 uint64_t host_binom(int a, int b) {
   if (b < 0 || b > a) return 0;
   unsigned __int128 r = 1;
@@ -277,19 +292,36 @@ extern "C" int haf_lowrank_c128(const double* G, int64_t n64, int64_t r64, doubl
   off += al((size_t)blocks_sum * 5 * sizeof(double));
   const size_t o_out = off;
   off += 256;
-  e = cudaMalloc(&dbuf, off);
-  if (e != cudaSuccess) return lfail(HAF_ENOMEM, std::string("haf_lowrank_c128: ") + cudaGetErrorString(e));
-  cudaStream_t st;
-  e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  std::lock_guard<std::mutex> lk(g_lr_mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  LrDevice& ld = g_lr_dev[dev];
+  if (!ld.st) {
+    e = cudaStreamCreateWithFlags(&ld.st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      ld.st = nullptr;
+      return lfail(HAF_ECUDA, std::string("haf_lowrank_c128: ") + cudaGetErrorString(e));
+    }
+  }
+  if (ld.bytes < off) {
+    if (ld.buf) cudaFree(ld.buf);
+    ld.buf = nullptr;
+    ld.bytes = 0;
+    e = cudaMalloc(&ld.buf, off);
+    if (e != cudaSuccess) return lfail(HAF_ENOMEM, std::string("haf_lowrank_c128: ") + cudaGetErrorString(e));
+    ld.bytes = off;
+  }
+  dbuf = ld.buf;
+  cudaStream_t st = ld.st;
   auto done = [&](int rc) {
-    cudaStreamDestroy(st);
-    cudaFree(dbuf);
+    if (ld.bytes > kLrKeepBytes) {  // do not hold a large expansion's memory
+      cudaStreamSynchronize(st);
+      cudaFree(ld.buf);
+      ld.buf = nullptr;
+      ld.bytes = 0;
+    }
     return rc;
   };
-  if (e != cudaSuccess) {
-    cudaFree(dbuf);
-    return lfail(HAF_ECUDA, std::string("haf_lowrank_c128: ") + cudaGetErrorString(e));
-  }
   zc* z[2] = {(zc*)(dbuf + o_z0), (zc*)(dbuf + o_z1)};
   double* za[2] = {(double*)(dbuf + o_a0), (double*)(dbuf + o_a1)};
   const zc one{1.0, 0.0};
@@ -302,8 +334,7 @@ extern "C" int haf_lowrank_c128(const double* G, int64_t n64, int64_t r64, doubl
   if (e != cudaSuccess) return done(lfail(HAF_ECUDA, std::string("haf_lowrank_c128: ") + cudaGetErrorString(e)));
   const zc* gdev = (const zc*)(dbuf + o_g);
   const uint64_t* bdev = (const uint64_t*)(dbuf + o_b);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
+  int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int cur = 0;
   int64_t launches = 0;
