@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) of one launch of the dominant subset kernel at
 # n = 48, from the ncu capture in profiles/subset_kernel_complex_n48_dram.md;
 # re-capture when the kernel changes.
-TRAFFIC_BYTES = {48: 1735424 + 0}
+TRAFFIC_BYTES = {48: 1645568 + 0}
 
 
 def metric_name(n: int) -> str:
