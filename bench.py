@@ -478,15 +478,17 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks.summary(),
         }
-        if args.gbs_batch > 0:
+        # the single-GPU legs run at N = 1 only (a scaling run reports the
+        # headline metric alone)
+        if args.gbs_batch > 0 and world == 1:
             line["batched"] = batched_leg(args.gbs_batch, args.seed)
-        if args.serve_requests > 0:
+        if args.serve_requests > 0 and world == 1:
             line["serving"] = serving_leg(args.serve_requests, args.serve_nmax, args.seed)
         if not args.no_precision and world == 1:
             line["lowrank"] = lowrank_leg(args.seed)
             line["precision"] = precision_leg(args.seed, (complex(res[0] + res[2], res[1] + res[3]), float(res[4]),
                                                           ms_step * 1e-3))
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(n, args.seed)
         print(json.dumps(line), flush=True)
     if world > 1:
