@@ -278,7 +278,9 @@ int haf_batched_tune(const double* const* As, const int64_t* ns, int64_t count, 
  *   poll         : waits up to timeout_us (< 0: no limit) for the ticket; out
  *                  = 2 doubles; info->seconds = latency from submit to the
  *                  result.  A ticket is collected once (then HAF_ENOTFOUND).
- *   destroy      : lets in-flight work finish, then frees everything.
+ *   destroy      : stops admitting and publishing work, lets the chunks
+ *                  already handed to the GPU finish, then frees everything
+ *                  (results not yet collected are lost).
  * The resident kernel exits once no warp has claimed a chunk for idle_us,
  * and the scheduler relaunches it when work arrives; no device wait is
  * unbounded.  create fails with HAF_EINVAL for max_jobs > 65535 or
