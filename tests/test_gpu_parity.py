@@ -219,6 +219,18 @@ def test_terms_against_oracle(n, loops):
     assert np.all(np.abs(got - want) <= 1e-9 * scale + 1e-300), np.max(np.abs(got - want) / scale)
 
 
+@pytest.mark.parametrize("loops", [False, True])
+def test_terms_at_n48_on_thousands_of_subsets(loops):
+    """2000 uniformly random subsets at the benchmark size n = 48, in the
+    launch shape the benchmark uses, against the binary128 oracle."""
+    A = inputs.complex_gaussian_symmetric(48, 4848)
+    masks = inputs.random_masks(24, 2000, seed=48 + int(loops))
+    got = hg.haf_terms(A, masks, loops)
+    want = oracle.terms(A, loops, masks)
+    rel = np.abs(got - want) / np.abs(want)
+    assert rel.max() <= 1e-9, (rel.max(), np.median(rel))
+
+
 def test_terms_sum_to_total():
     n = 16
     h = n // 2
