@@ -15,7 +15,16 @@ Printed (rank 0, one JSON line):
           over the measured step time, against the FP64 DFMA rate measured
           live on the same GPU by the library's probe kernel;
   cpu_baseline  the binary128 CPU oracle on a bounded sample of the same
-          workload's subsets, on the host's cores.
+          workload's subsets, on the host's cores;
+  batched  4096 GBS-shaped submatrices (n even in [8, 32]) in one
+          graph-captured launch sequence, against one call per matrix;
+  serving  a Poisson stream of haf/lhaf GBS requests through the
+          continuous-batching server (capacity, p50/p99), against one
+          synchronous call per request (capacity and FIFO latency);
+  precision  the FP32-bulk mode against FP64 at n = 40 and 48 (error
+          relative to sum |f(Z)| and to |haf|, speed-up);
+  lowrank  the App. C expansion at n = 56, r = 4, 6, 8.
+The last five legs run at N = 1 only.
 Multi-GPU (torchrun): each rank computes its own hafnian (independent
 problems, no collective on the data path): weak scaling.
 ``--impl reference``: the oracle itself, timed on the host cores (rank 0).
