@@ -1,0 +1,66 @@
+"""Host-side logic of bench.py, on the CPU: the algorithmic flop count the
+roofline divides by, the clock-record summary, the HBM peak lookup, and the
+reference arm's JSON line (the oracle timed on the host cores)."""
+import json
+import os
+import subprocess
+import sys
+from math import comb
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+@pytest.mark.parametrize("n", list(range(2, 58, 2)))
+def test_alg_flops_is_the_sum_over_subset_sizes(n):
+    """(40/3 + 4/3) N^3 real flops per subset of N = 2m rows, summed over
+    the C(h, m) subsets of each size, against the closed form."""
+    h = n // 2
+    direct = sum(comb(h, m) * (44 * (2 * m) ** 3) for m in range(h + 1)) / 3
+    assert bench.alg_flops(n) == pytest.approx(direct, rel=1e-15)
+
+
+def test_alg_flops_at_the_benchmark_size():
+    # 2^24 subsets, (44/3) 2^24 24^2 27 = 3.826e12 flops
+    assert bench.alg_flops(48) == pytest.approx(3.8268e12, rel=1e-4)
+
+
+def test_clock_summary():
+    s = bench.ClockSampler(0)
+    s.samples = [["2070", "2070", "900.1", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+                 ["2055", "2070", "1300.0", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+                 ["1980", "2070", "1390.5", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+                 ["[N/A]"]]
+    out = s.summary()
+    assert out["sm_mhz"] == 2055 and out["sm_max_mhz"] == 2070
+    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 4
+
+
+def test_hbm_peak_is_a_positive_figure():
+    assert bench.hbm_peak_gbs() > 1000
+
+
+def test_reference_arm_prints_the_contract_line():
+    env = dict(os.environ, RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "16",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["unit"] == "subset-terms/s" and line["higher_is_better"]
+    assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["metric"] == bench.metric_name(16)
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    env = dict(os.environ, RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "16",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=120, env=env)
+    assert r.returncode == 0 and r.stdout.strip() == ""
