@@ -221,13 +221,17 @@ def test_terms_against_oracle(n, loops):
 
 @pytest.mark.parametrize("loops", [False, True])
 def test_terms_at_n48_on_thousands_of_subsets(loops):
-    """2000 uniformly random subsets at the benchmark size n = 48, in the
-    launch shape the benchmark uses, against the binary128 oracle."""
+    """5000 uniformly random subsets at the benchmark size n = 48 (10^4
+    over haf and lhaf), in the launch shape the benchmark uses, against the
+    binary128 oracle."""
     A = inputs.complex_gaussian_symmetric(48, 4848)
-    masks = inputs.random_masks(24, 2000, seed=48 + int(loops))
+    masks = inputs.random_masks(24, 5000, seed=48 + int(loops))
+    masks = masks[masks != 0]  # f(empty set) = 0 has no relative error
     got = hg.haf_terms(A, masks, loops)
     want = oracle.terms(A, loops, masks)
     rel = np.abs(got - want) / np.abs(want)
+    print(f"n=48 loops={loops} subsets={masks.size}: max rel {rel.max():.3g}, "
+          f"p99.9 {np.quantile(rel, 0.999):.3g}, median {np.median(rel):.3g}")
     assert rel.max() <= 1e-9, (rel.max(), np.median(rel))
 
 
