@@ -156,6 +156,22 @@ def test_all_ones_large(n):
     assert _close(got.value, want, got.abs_sum)
 
 
+@pytest.mark.parametrize("n", [24, 40])
+def test_rank_one_closed_forms(n):
+    """A = x x^T with complex x: haf = (n-1)!! prod x_i; with the diagonal
+    replaced by x, lhaf = T(n) prod x_i (every single-pair matching has
+    weight prod x_i)."""
+    g = inputs.rng(7200 + n)
+    x = (g.standard_normal(n) + 1j * g.standard_normal(n)) / np.sqrt(2)
+    A = np.outer(x, x)
+    p = complex(np.prod(x))
+    got = hg.haf_info(A)
+    assert _close(got.value, oracle.double_factorial(n - 1) * p, got.abs_sum)
+    np.fill_diagonal(A, x)
+    got = hg.haf_info(A, loops=True)
+    assert _close(got.value, oracle.telephone(n) * p, got.abs_sum)
+
+
 def test_maximum_size_exact_values():
     """HAF_MAX_N = 56: haf(J_56) = 55!! and lhaf(J_52) = T(52) (real path,
     the size the library is specified up to; about a minute of GPU time)."""

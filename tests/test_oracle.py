@@ -132,6 +132,37 @@ def test_formula_all_ones(n):
     assert abs(got - oracle.telephone(n)) <= 1e-20 * oracle.telephone(n) + 0.5
 
 
+@pytest.mark.parametrize("n", [8, 16, 20])
+def test_formula_rank_one_closed_forms(n):
+    """A = x x^T with complex x: every perfect matching has weight prod x_i,
+    so haf = (n-1)!! prod x_i (eq. haf1).  With the diagonal replaced by x,
+    every single-pair matching has weight prod x_i too, so lhaf = T(n) prod x_i
+    (eq. haf2).  Pins the formula with complex entries beyond brute force."""
+    g = inputs.rng(7000 + n)
+    x = (g.standard_normal(n) + 1j * g.standard_normal(n)) / np.sqrt(2)
+    A = np.outer(x, x)
+    p = np.prod(x)
+    got, _ = oracle.haf_formula(A)
+    want = oracle.double_factorial(n - 1) * p
+    assert abs(got - want) <= 1e-13 * abs(want)
+    np.fill_diagonal(A, x)
+    got, _ = oracle.haf_formula(A, True)
+    want = oracle.telephone(n) * p
+    assert abs(got - want) <= 1e-13 * abs(want)
+
+
+def test_formula_lhaf_of_a_diagonal_matrix():
+    """Only the all-loops matching survives: lhaf(diag(d)) = prod d_i, and
+    haf(diag(d)) = 0 (the loop series alone, Sec. 3.3)."""
+    n = 20
+    g = inputs.rng(7100)
+    d = g.standard_normal(n) + 1j * g.standard_normal(n)
+    got, _ = oracle.haf_formula(np.diag(d), True)
+    assert abs(got - np.prod(d)) <= 1e-13 * abs(np.prod(d))
+    got, _ = oracle.haf_formula(np.diag(d))
+    assert got == 0
+
+
 def test_formula_zero_size():
     assert oracle.haf_formula(np.zeros((0, 0)))[0] == 1
 
