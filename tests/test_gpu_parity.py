@@ -173,12 +173,12 @@ def test_rank_one_closed_forms(n):
 
 
 def test_maximum_size_exact_values():
-    """HAF_MAX_N = 56: haf(J_56) = 55!! and lhaf(J_52) = T(52) (real path,
-    the size the library is specified up to; about a minute of GPU time)."""
+    """HAF_MAX_N = 56: haf(J_56) = 55!! and lhaf(J_56) = T(56) (real path,
+    the size the library is specified up to; about 1.5 minutes of GPU time)."""
     got = hg.haf_info(np.ones((56, 56)), real=True)
     assert _close(got.value, oracle.double_factorial(55), got.abs_sum)
-    got = hg.haf_info(np.ones((52, 52)), loops=True, real=True)
-    assert _close(got.value, oracle.telephone(52), got.abs_sum)
+    got = hg.haf_info(np.ones((56, 56)), loops=True, real=True)
+    assert _close(got.value, oracle.telephone(56), got.abs_sum)
 
 
 @pytest.mark.parametrize("loops", [False, True])
