@@ -156,6 +156,25 @@ def test_all_ones_large(n):
     assert _close(got.value, want, got.abs_sum)
 
 
+def test_accuracy_experiment_on_known_graphs():
+    """The accuracy experiment of Sec. 4 (eq. error): complete graphs without
+    and with loops, (n-1)!! and T(n), and complete bipartite graphs, (n/2)!,
+    for n = 4, 8, ..., 48 in the real path.  The error relative to the exact
+    count grows with n as sum_Z |f(Z)| does (about 8e11 times the count at
+    n = 48); relative to sum_Z |f(Z)| it stays at the level of FP64 rounding
+    within one summand, so the double-double sum adds no error."""
+    from math import factorial
+    for n in range(4, 49, 4):
+        J = np.ones((n, n))
+        Bp = np.ascontiguousarray(inputs.bipartite(np.ones((n // 2, n // 2))).real)
+        for M, loops, exact in ((J, False, oracle.double_factorial(n - 1)), (J, True, oracle.telephone(n)),
+                                (Bp, False, factorial(n // 2))):
+            r = hg.haf_info(M, loops=loops, real=True)
+            err = abs(r.value.real - exact)
+            assert r.value.imag == 0
+            assert err <= 1e-13 * r.abs_sum, (n, loops, err / r.abs_sum)
+
+
 @pytest.mark.parametrize("n", [24, 40])
 def test_rank_one_closed_forms(n):
     """A = x x^T with complex x: haf = (n-1)!! prod x_i; with the diagonal
