@@ -135,7 +135,7 @@ def cpu_baseline(n: int, seed: int, budget_s: float = 12.0):
 
 
 def batched_leg(count: int, seed: int, reps: int = 3):
-    """GBS-shaped batch (config 2): ``count`` submatrices of a 32-mode kernel
+    """GBS-shaped batch: ``count`` submatrices of a 32-mode kernel
     B = U diag(tanh 0.88) U^T with total photons uniform on even n in
     [8, 32], in one graph-captured persistent launch, against one launch per
     hafnian through the host entry point; both on this GPU."""
@@ -170,7 +170,7 @@ def batched_leg(count: int, seed: int, reps: int = 3):
 
 
 def precision_leg(seed: int, value48=None):
-    """Precision study (config 3 shape): FP32-bulk mode against FP64 at n = 40
+    """Precision study: FP32-bulk mode against FP64 at n = 40
     and 48 on a complex Gaussian matrix and on a GBS submatrix (haf).  Errors
     of the values are relative to abs_sum = sum_Z |f(Z)| (the stated form) and
     to |haf|; sampled summands of the two modes against each other (the
@@ -204,7 +204,7 @@ def precision_leg(seed: int, value48=None):
                          "err_over_abs_value": d / max(abs(v64), 1e-300), "abs_value_over_abs_sum": abs(v64) / a64,
                          "s_fp64": t64, "s_fp32": t32, "speedup": t64 / t32,
                          "term_rel_err_median": float(np.median(rel)), "term_rel_err_max": float(rel.max())})
-    return {"workload": "haf, n = 40 and 48, complex Gaussian (config 0 recipe) and GBS submatrix (config 2 recipe); "
+    return {"workload": "haf, n = 40 and 48, complex Gaussian symmetric and GBS submatrix of a 32-mode kernel (r = 0.88); "
                         "FP32 bulk (single-precision Householder + La Budde) vs FP64; 1024 sampled summands per case",
             "stated_tol_over_abs_sum": hg.HAF_FP32_REL_TOL, "rows": rows}
 
@@ -250,7 +250,7 @@ def hbm_peak_gbs() -> float:
 
 
 def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
-    """Serving (config 4 shape, scaled): haf/lhaf requests (50/50) on GBS
+    """Serving: haf/lhaf requests (50/50) on GBS
     submatrices, n even in [8, n_max] with P(n) proportional to 2^(-n/8),
     through the continuous-batching server.  The capacity is measured first
     with all requests submitted at once; the open-loop run then offers

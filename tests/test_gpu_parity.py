@@ -23,7 +23,7 @@ def _close(got, want, scale, tol=TOL):
 
 
 # ------------------------------------------------------------- n = 16 -------
-def test_config0_complex16_haf_against_brute_force():
+def test_complex16_haf_against_brute_force():
     A = inputs.complex_gaussian_symmetric(16, 0)
     want = oracle.haf_brute(A)
     _, scale = oracle.haf_formula(A)
@@ -33,7 +33,7 @@ def test_config0_complex16_haf_against_brute_force():
     assert r.subsets == 2 ** 8 - 1
 
 
-def test_config0_complex16_lhaf_against_oracle():
+def test_complex16_lhaf_against_oracle():
     A = inputs.complex_gaussian_symmetric(16, 0)
     want, scale = oracle.haf_formula(A, True)
     r = hg.haf_info(A, loops=True)
