@@ -214,6 +214,26 @@ def test_formula_block_diagonal_factorises():
         assert abs(got - want) <= 1e-13 * abs(want)
 
 
+def test_formula_permuted_block_diagonal_n24():
+    """haf(P (A + C) P^T) = haf(A) haf(C) for two random complex 12 x 12
+    blocks under a random vertex permutation P (Sec. 2; any pairing works,
+    Sec. 3.2), and the same for lhaf.  The permutation puts vertices of both
+    blocks into the same pairs, so the subset sum does not factorise term by
+    term; the expected value comes from brute force on each block.  This
+    pins the formula on fully random complex input at n = 24."""
+    A = inputs.complex_gaussian_symmetric(12, 23)
+    C = inputs.complex_gaussian_symmetric(12, 24)
+    M = np.zeros((24, 24), dtype=complex)
+    M[:12, :12] = A
+    M[12:, 12:] = C
+    perm = inputs.rng(25).permutation(24)
+    M = M[np.ix_(perm, perm)]
+    for loops in (False, True):
+        want = oracle.haf_brute(A, loops) * oracle.haf_brute(C, loops)
+        got, s = oracle.haf_formula(M, loops)
+        assert abs(got - want) <= 1e-14 * abs(want), (loops, got, want, s)
+
+
 def test_terms_sum_to_formula():
     """The per-subset entry point gives the same summands (signed sum)."""
     n = 12
