@@ -25,6 +25,9 @@ CASES = [
     ("rgauss28_haf", 28, 128, False, True),
     ("rgauss28_lhaf", 28, 128, True, True),
     ("cgauss32_haf", 32, 32, False, False),
+    ("cgauss32_lhaf", 32, 32, True, False),
+    ("cgauss36_haf", 36, 36, False, False),
+    ("cgauss36_lhaf", 36, 36, True, False),
 ]
 
 

@@ -306,3 +306,23 @@ def test_lowrank_monomial_count():
     count = sum(1 for a in range(0, n2 + 1, 2) for b in range(0, n2 + 1 - a, 2)
                 if (n2 - a - b) % 2 == 0)
     assert count == comb(n2 // 2 + r - 1, r - 1)
+
+
+# ------------------------------------------------------ stored values ----
+def test_stored_oracle_values_come_from_the_oracle():
+    """tests/golden/oracle_values.json is written by make_golden.py, which
+    calls only the oracle.  Recomputing its cheapest case (real n = 28, haf)
+    reproduces the stored value and abs_sum; every case's inputs are the
+    seeded generators' and its sizes are even and within the formula's range."""
+    import json
+    with open(os.path.join(GOLDEN, "oracle_values.json")) as f:
+        cases = json.load(f)["cases"]
+    names = [c["name"] for c in cases]
+    assert len(set(names)) == len(names)
+    for c in cases:
+        assert c["n"] % 2 == 0 and 2 <= c["n"] <= 48 and c["abs_sum"] > 0
+    c = next(c for c in cases if c["name"] == "rgauss28_haf")
+    A = inputs.real_gaussian_symmetric(c["n"], c["seed"])
+    v, s = oracle.haf_formula(A, c["loops"])
+    assert abs(v - complex(c["re"], c["im"])) <= 1e-15 * s
+    assert abs(s - c["abs_sum"]) <= 1e-14 * s
