@@ -5,7 +5,10 @@ Every number in the file comes from ``oracle`` (the binary128 CPU oracle)
 applied to inputs from ``paper_1805_12498_gb300.inputs``; nothing here calls
 the CUDA library.
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py [--missing-only]
+
+``--missing-only`` keeps the stored cases whose parameters are unchanged and
+computes only the others.
 """
 import json
 import os
@@ -28,6 +31,10 @@ CASES = [
     ("cgauss32_lhaf", 32, 32, True, False),
     ("cgauss36_haf", 36, 36, False, False),
     ("cgauss36_lhaf", 36, 36, True, False),
+    ("rgauss32_haf", 32, 132, False, True),
+    ("rgauss32_lhaf", 32, 132, True, True),
+    ("rgauss36_haf", 36, 136, False, True),
+    ("rgauss36_lhaf", 36, 136, True, True),
 ]
 
 
@@ -35,7 +42,16 @@ def main():
     out = {"source": "oracle.haf_formula (binary128), inputs.complex_gaussian_symmetric / "
                      "inputs.real_gaussian_symmetric with the listed seeds",
            "cases": []}
+    stored = {}
+    path = os.path.join(HERE, "oracle_values.json")
+    if "--missing-only" in sys.argv and os.path.exists(path):
+        with open(path) as f:
+            stored = {c["name"]: c for c in json.load(f)["cases"]}
     for name, n, seed, loops, real in CASES:
+        c = stored.get(name)
+        if c and (c["n"], c["seed"], c["loops"], c["real"]) == (n, seed, loops, real):
+            out["cases"].append(c)
+            continue
         A = (inputs.real_gaussian_symmetric(n, seed) if real
              else inputs.complex_gaussian_symmetric(n, seed))
         t = time.time()
@@ -43,7 +59,7 @@ def main():
         out["cases"].append({"name": name, "n": n, "seed": seed, "loops": loops, "real": real,
                              "re": v.real, "im": v.imag, "abs_sum": s})
         print(name, v, s, f"{time.time() - t:.1f}s", flush=True)
-    with open(os.path.join(HERE, "oracle_values.json"), "w") as f:
+    with open(path, "w") as f:
         json.dump(out, f, indent=1)
 
 

@@ -3,6 +3,9 @@ Householder reduction, loop moments and La Budde recurrence, FP64 series
 and double-double subset sum.  Its error is stated relative to
 abs_sum = sum_Z |f(Z)| (HAF_FP32_REL_TOL) and checked against the oracle
 (small n) and against the FP64 path (which the oracle pins) at larger n."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -46,6 +49,22 @@ def test_fp32_against_fp64(n):
             b = hg.haf_info(A, loops, precision="fp32")
             assert abs(a.value - b.value) <= TOL32 * a.abs_sum, (n, loops)
             assert b.abs_sum == pytest.approx(a.abs_sum, rel=1e-4)
+
+
+def test_fp32_against_stored_oracle_sums():
+    """The FP32 mode against the full binary128 oracle sums that the FP64
+    parity tests use (tests/golden/oracle_values.json: n = 28-36, complex
+    and real, haf and lhaf), within the stated HAF_FP32_REL_TOL * sum |f|."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_values.json")
+    with open(path) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        A = (inputs.real_gaussian_symmetric(c["n"], c["seed"]) if c["real"]
+             else inputs.complex_gaussian_symmetric(c["n"], c["seed"]))
+        got = hg.haf_info(A, loops=c["loops"], real=c["real"], precision="fp32")
+        want = complex(c["re"], c["im"])
+        assert abs(got.value - want) <= TOL32 * c["abs_sum"], (c["name"], got.value, want, c["abs_sum"])
+        assert got.abs_sum == pytest.approx(c["abs_sum"], rel=1e-4), c["name"]
 
 
 def test_fp32_terms_at_n48_against_oracle():
