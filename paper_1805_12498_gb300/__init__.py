@@ -24,7 +24,7 @@ from . import _native, tuning
 from ._native import HAF_FLAG_FP32, HAF_FLAG_LOOPS, HAF_FLAG_REAL, HAF_MAX_N, HafError  # noqa: F401
 
 __all__ = ["haf", "lhaf", "haf_info", "haf_batched", "haf_terms", "workspace_bytes",
-           "haf_launch", "haf_part", "part_subsets", "combine", "Server", "fp64_peak", "tune",
+           "haf_launch", "haf_launch_noalloc", "haf_part", "part_subsets", "combine", "Server", "fp64_peak", "tune",
            "tune_set", "batched_tune", "haf_lowrank", "HafError", "HAF_MAX_N", "HAF_FP32_MAX_N", "HAF_FP32_REL_TOL"]
 
 # FP32-bulk mode: offered for n <= HAF_FP32_MAX_N (include/hafnian_gb300.h)
@@ -144,6 +144,17 @@ def haf_launch(dA_ptr: int, n: int, d_out_ptr: int, d_work_ptr: int, ws_bytes: i
     tuning.ensure_loaded()
     flags = _flags(loops, real, precision)
     _native.check(_native.lib().haf_launch(dA_ptr, n, flags, d_out_ptr, d_work_ptr, ws_bytes, stream_ptr))
+
+
+def haf_launch_noalloc(dA_ptr: int, n: int, d_out_ptr: int, stream_ptr: int = 0, loops: bool = False,
+                       real: bool = False) -> None:
+    """Allocation-free form of ``haf_launch`` (FP64), for callers that may
+    not allocate device memory at call time: the library's one static device
+    scratch array takes the place of the workspace, and no call allocates.
+    Calls that overlap on the GPU share that array and race, so keep them on
+    one stream.  The same 5-double record lands at d_out_ptr."""
+    flags = _flags(loops, real)
+    _native.check(_native.lib().haf_launch_noalloc(dA_ptr, n, flags, d_out_ptr, stream_ptr))
 
 
 def haf_part(A, part: int, nparts: int, loops: bool = False, real: bool | None = None,

@@ -86,6 +86,9 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         L.haf_launch.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
         L.haf_launch.restype = ctypes.c_int
+        L.haf_launch_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p,
+                                         ctypes.c_void_p]
+        L.haf_launch_noalloc.restype = ctypes.c_int
         L.haf_terms_c128.argtypes = [_DP, ctypes.c_int64, ctypes.c_int, _U64P, ctypes.c_int64, _DP]
         L.haf_terms_c128.restype = ctypes.c_int
         L.haf_terms.argtypes = [_DP, ctypes.c_int64, ctypes.c_uint32, _U64P, ctypes.c_int64, _DP]

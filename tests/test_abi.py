@@ -79,3 +79,17 @@ def test_precision_limits_match_the_header():
     assert int(re.search(r"#define HAF_FLAG_FP32 \(1u << (\d+)\)", src).group(1)) == 2
     with pytest.raises(ValueError):
         hg._flags(precision="fp16")
+
+
+def test_noalloc_binding_checks_arguments_without_gpu_work():
+    """The Python form of haf_launch_noalloc passes its arguments through;
+    the library rejects bad sizes and null pointers before any CUDA call."""
+    import paper_1805_12498_gb300 as hg
+    from paper_1805_12498_gb300 import _native
+    for bad_n in (0, 7, 58):
+        with pytest.raises(hg.HafError) as e:
+            hg.haf_launch_noalloc(0, bad_n, 0)
+        assert e.value.code == _native.HAF_EINVAL and "HAF_MAX_N" in str(e.value)
+    with pytest.raises(hg.HafError) as e:
+        hg.haf_launch_noalloc(0, 8, 0, loops=True)
+    assert e.value.code == _native.HAF_EINVAL and "null pointer" in str(e.value)
