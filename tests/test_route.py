@@ -35,9 +35,10 @@ def submatrix(A, mask, h):
 
 def labudde(H, h):
     """Coefficients d_0..d_h of det(I - lambda H) for upper Hessenberg H by
-    the recurrence on leading principal submatrices, truncated at degree h."""
+    the recurrence on leading principal submatrices, truncated at degree h
+    (in H's precision)."""
     N = H.shape[0]
-    D = [np.zeros(h + 1, dtype=complex) for _ in range(N + 1)]
+    D = [np.zeros(h + 1, dtype=H.dtype) for _ in range(N + 1)]
     D[0][0] = 1
     for i in range(1, N + 1):
         # D_i = (1 - lambda H_{i-1,i-1}) D_{i-1}
@@ -54,8 +55,13 @@ def labudde(H, h):
     return D[N]
 
 
-def summand(A, mask, h, loops):
+def summand(A, mask, h, loops, bulk=np.complex128):
+    """f(Z) by the kernels' route.  ``bulk`` is the precision of the gather,
+    the reflectors, the Hessenberg form, La Budde and the loop moments;
+    the series and the Cayley-Hamilton continuation run in complex128 on the
+    widened coefficients (complex64 models the FP32-bulk mode)."""
     B, v, X = submatrix(A, mask, h)
+    B, v, X = B.astype(bulk), v.astype(bulk), X.astype(bulk)
     N = B.shape[0]
     if N == 0:
         return 0.0
@@ -68,17 +74,18 @@ def summand(A, mask, h, loops):
         w = b.copy()
         w[0] += ph * nrm
         w = w / np.linalg.norm(w) * np.sqrt(2) if np.linalg.norm(w) > 0 else w
-        P = np.eye(N) - np.outer(w, w.conj())
+        P = np.eye(N, dtype=bulk) - np.outer(w, w.conj())
         B = P @ B @ P
         a = v @ P
         b = P @ b  # = -ph * nrm e_0
         H, Q = sl.hessenberg(B, calc_q=True)  # Q e_0 = e_0
         a = a @ Q
         b = Q.conj().T @ b
-        assert np.allclose(b[1:], 0, atol=1e-12 * max(1.0, nrm))
+        eps = np.finfo(bulk).eps
+        assert np.allclose(b[1:], 0, atol=1e4 * eps * max(1.0, nrm))
     else:
         H = sl.hessenberg(B)
-    d = labudde(H, h)
+    d = labudde(H, h).astype(np.complex128)
     # g = D^{-1/2}: k g_k = -sum_{j=1}^{min(k,N)} (k - j/2) d_j g_{k-j}
     g = np.zeros(h + 1, dtype=complex)
     g[0] = 1
@@ -89,7 +96,7 @@ def summand(A, mask, h, loops):
     u = np.zeros(h + 1, dtype=complex)
     y = b.copy()  # supported on e_0
     for k in range(1, min(h, N) + 1):
-        u[k] = a @ y
+        u[k] = complex(a @ y)  # widened, like the coefficients
         y = H @ y
     for k in range(N + 1, h + 1):  # Cayley-Hamilton: sum_j d_j u_{k-j} = 0
         u[k] = -sum(d[j] * u[k - j] for j in range(1, N + 1))
@@ -125,3 +132,24 @@ def test_labudde_is_the_characteristic_polynomial():
     for m in mu:
         want = np.convolve(want, [1.0, -m])
     assert np.allclose(d, want, atol=1e-10 * np.max(np.abs(want)))
+
+
+@pytest.mark.parametrize("n", [16, 20])
+@pytest.mark.parametrize("loops", [False, True])
+def test_single_precision_bulk_route_error(n, loops):
+    """The FP32-bulk arithmetic (complex64 bulk steps, complex128 series and
+    sum) over every subset of an n = 16 or 20 matrix, against the oracle's
+    full sum.  Its error relative to sum_Z |f(Z)| (about 1e-8 to 1.3e-7 on
+    these inputs) is checked at 1e-6, a hundredth of the FP32 mode's stated
+    bound (HAF_FP32_REL_TOL = 1e-4 in the C header).  The same route in
+    complex128 stays below 1e-12 (about 1e-16 here), inside the FP64
+    contract of 1e-10."""
+    import paper_1805_12498_gb300 as hg
+    h = n // 2
+    A = np.asarray(inputs.complex_gaussian_symmetric(n, 960 + n), dtype=complex)
+    want, scale = oracle.haf_formula(A, loops)
+    masks = range(1, 1 << h)
+    signs = [(-1) ** (h - bin(m).count("1")) for m in masks]
+    for bulk, bound in ((np.complex64, 1e-2 * hg.HAF_FP32_REL_TOL), (np.complex128, 1e-12)):
+        got = sum(sg * summand(A, m, h, loops, bulk) for sg, m in zip(signs, masks))
+        assert abs(got - want) <= bound * scale, (bulk.__name__, abs(got - want) / scale)
