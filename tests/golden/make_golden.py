@@ -35,6 +35,7 @@ CASES = [
     ("rgauss32_lhaf", 32, 132, True, True),
     ("rgauss36_haf", 36, 136, False, True),
     ("rgauss36_lhaf", 36, 136, True, True),
+    ("cgauss40_haf", 40, 40, False, False),
 ]
 
 

@@ -53,7 +53,7 @@ def test_fp32_against_fp64(n):
 
 def test_fp32_against_stored_oracle_sums():
     """The FP32 mode against the full binary128 oracle sums that the FP64
-    parity tests use (tests/golden/oracle_values.json: n = 28-36, complex
+    parity tests use (tests/golden/oracle_values.json: n = 28-40, complex
     and real, haf and lhaf), within the stated HAF_FP32_REL_TOL * sum |f|."""
     path = os.path.join(os.path.dirname(__file__), "golden", "oracle_values.json")
     with open(path) as f:
