@@ -36,6 +36,7 @@ CASES = [
     ("rgauss36_haf", 36, 136, False, True),
     ("rgauss36_lhaf", 36, 136, True, True),
     ("cgauss40_haf", 40, 40, False, False),
+    ("rgauss40_haf", 40, 140, False, True),
 ]
 
 
