@@ -21,6 +21,9 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import oracle  # noqa: E402
 from paper_1805_12498_gb300 import inputs  # noqa: E402
 
+sys.path.insert(0, HERE)
+import cases  # noqa: E402
+
 CASES = [
     # (name, n, seed, loops, real)
     ("cgauss28_haf", 28, 28, False, False),
@@ -40,27 +43,45 @@ CASES = [
 ]
 
 
+def recipe_cases():
+    """(name, params, matrix, loops) of every stored case: the complex and
+    real Gaussian sweep above, the GBS submatrices and the large requests of
+    the server mix (tests/golden/cases.py)."""
+    for name, n, seed, loops, real in CASES:
+        A = (inputs.real_gaussian_symmetric(n, seed) if real
+             else inputs.complex_gaussian_symmetric(n, seed))
+        yield name, {"n": n, "seed": seed, "loops": loops, "real": real}, A, loops
+    for name, n, seed, loops in cases.GBS_CASES:
+        yield name, {"n": n, "seed": seed, "loops": loops, "real": False, "recipe": "gbs_submatrix"}, \
+            cases.gbs_submatrix(n, seed), loops
+    for k, M, loops in cases.server_mix_stored(11):
+        yield f"server11_req{k}", {"n": M.shape[0], "seed": 11, "loops": loops, "real": False,
+                                   "recipe": f"server_mix[{k}]"}, cases.pad_odd(M), loops
+
+
 def main():
     out = {"source": "oracle.haf_formula (binary128), inputs.complex_gaussian_symmetric / "
-                     "inputs.real_gaussian_symmetric with the listed seeds",
+                     "inputs.real_gaussian_symmetric with the listed seeds, and the recipes of "
+                     "tests/golden/cases.py (GBS submatrices, the server mix)",
            "cases": []}
     stored = {}
     path = os.path.join(HERE, "oracle_values.json")
     if "--missing-only" in sys.argv and os.path.exists(path):
         with open(path) as f:
             stored = {c["name"]: c for c in json.load(f)["cases"]}
-    for name, n, seed, loops, real in CASES:
+    for name, params, A, loops in recipe_cases():
         c = stored.get(name)
-        if c and (c["n"], c["seed"], c["loops"], c["real"]) == (n, seed, loops, real):
+        if c and all(c.get(k) == v for k, v in params.items()):
             out["cases"].append(c)
             continue
-        A = (inputs.real_gaussian_symmetric(n, seed) if real
-             else inputs.complex_gaussian_symmetric(n, seed))
         t = time.time()
         v, s = oracle.haf_formula(A, loops)
-        out["cases"].append({"name": name, "n": n, "seed": seed, "loops": loops, "real": real,
-                             "re": v.real, "im": v.imag, "abs_sum": s})
+        out["cases"].append({"name": name, **params, "re": v.real, "im": v.imag, "abs_sum": s})
         print(name, v, s, f"{time.time() - t:.1f}s", flush=True)
+        with open(path, "w") as f:
+            json.dump(out | {"cases": out["cases"] + [c for nm, c in stored.items()
+                                                      if nm not in {x["name"] for x in out["cases"]}]},
+                      f, indent=1)
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
 

@@ -12,6 +12,8 @@ import oracle
 import paper_1805_12498_gb300 as hg
 from paper_1805_12498_gb300 import inputs
 
+from golden import cases as golden_cases
+
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
@@ -85,8 +87,7 @@ def test_golden_oracle_values():
     with open(GOLDEN) as f:
         cases = json.load(f)["cases"]
     for c in cases:
-        A = (inputs.real_gaussian_symmetric(c["n"], c["seed"]) if c["real"]
-             else inputs.complex_gaussian_symmetric(c["n"], c["seed"]))
+        A = golden_cases.case_matrix(c)
         got = hg.haf_info(A, loops=c["loops"], real=c["real"])
         want = complex(c["re"], c["im"])
         assert _close(got.value, want, c["abs_sum"]), (c["name"], got.value, want)
@@ -219,8 +220,9 @@ def test_block_diagonal_factorises():
     M[:10, :10] = A
     M[10:, 10:] = C
     for loops in (False, True):
-        a, c, m = hg.haf_info(A, loops), hg.haf_info(C, loops), hg.haf_info(M, loops)
-        assert _close(m.value, a.value * c.value, m.abs_sum)
+        (a, _), (c, _) = oracle.haf_formula(A, loops), oracle.haf_formula(C, loops)
+        m = hg.haf_info(M, loops)
+        assert _close(m.value, a * c, m.abs_sum), (loops, m.value, a * c)
 
 
 def test_permutation_and_scaling_invariance():
@@ -282,39 +284,59 @@ def test_terms_sum_to_total():
 
 
 # ------------------------------------------------ batch / device forms -----
-def test_batched_matches_single():
+def _oracle(M, loops):
+    """(value, sum |f|) of the oracle for the size the library evaluates:
+    at test time up to n = 24, else the stored oracle sum of that case."""
+    n = golden_cases.evaluated_size(M.shape[0], loops)
+    if n == 0:
+        return (0j if M.shape[0] else 1 + 0j), (0.0 if M.shape[0] else 1.0)
+    return oracle.haf_formula(golden_cases.pad_odd(M), loops)
+
+
+def test_batched_matches_single_and_oracle():
     mats = [inputs.complex_gaussian_symmetric(n, 300 + i) for i, n in
             enumerate([8, 16, 22, 2, 0, 5, 14, 20, 12, 18])]
     for loops in (False, True):
         vals, infos = hg.haf_batched(mats, loops=loops, with_info=True)
         for M, v, inf in zip(mats, vals, infos):
-            single = hg.haf_info(M, loops) if M.shape[0] > 0 else None
-            if single is None:
-                assert v == 1
-                continue
-            assert _close(v, single.value, max(single.abs_sum, 1e-300)), (M.shape, loops)
+            want, scale = _oracle(M, loops)
+            assert _close(v, want, max(scale, 1e-300)), (M.shape, loops, v, want)
+            if M.shape[0] > 0:
+                single = hg.haf_info(M, loops)
+                assert _close(v, single.value, max(single.abs_sum, 1e-300)), (M.shape, loops)
 
 
 def test_gbs_batch_engine_replay_and_oracle():
     """A GBS-shaped batch (repeated rows/columns of U diag(tanh r) U^T):
-    first call builds the plan and graph, the second replays it with new
-    inputs of the same sizes; both agree with single calls, and a sample
-    agrees with the oracle."""
+    the first call builds the plan and graph, the second replays it with
+    new inputs of the same sizes; every result of both against the oracle."""
     B, mats = inputs.gbs_batch(48, seed=5, n_min=2, n_max=20)
-    _, mats2 = inputs.gbs_batch(48, seed=6, n_min=2, n_max=20)
     sizes = [M.shape[0] for M in mats]
     mats2 = [inputs.repeat_submatrix(B, np.bincount(inputs.rng(7 + i).integers(0, 32, size=n), minlength=32))
              for i, n in enumerate(sizes)]
     for batch in (mats, mats2):
         for loops in (False, True):
-            vals, infos = hg.haf_batched(batch, loops=loops, with_info=True)
-            for M, v, inf in zip(batch, vals, infos):
-                single = hg.haf_info(M, loops)
-                assert _close(v, single.value, max(single.abs_sum, 1e-300))
-    for M, v in list(zip(mats, hg.haf_batched(mats)))[:12]:
-        if M.shape[0] <= 16:
-            want, scale = oracle.haf_formula(M)
-            assert _close(v, want, max(scale, 1e-300))
+            vals = hg.haf_batched(batch, loops=loops)
+            for M, v in zip(batch, vals):
+                want, scale = _oracle(M, loops)
+                assert _close(v, want, max(scale, 1e-300)), (M.shape[0], loops, v, want)
+
+
+def test_gbs_batch_at_the_large_end_against_stored_oracle_sums():
+    """The batched form at the top of the GBS batch's size range (n = 28 and
+    32, haf and lhaf) among small matrices, each result against the full
+    binary128 oracle sum (stored for n > 24, at test time below)."""
+    for loops in (False, True):
+        big = [(name, n, seed) for name, n, seed, lp in golden_cases.GBS_CASES if lp == loops]
+        mats = [golden_cases.gbs_submatrix(n, seed) for _, n, seed in big]
+        small = [golden_cases.gbs_submatrix(n, 700 + n) for n in (8, 12, 16, 20, 24)]
+        vals = hg.haf_batched(mats + small, loops=loops)
+        for (name, _, _), v in zip(big, vals[:len(big)]):
+            want, scale = golden_cases.stored(name)
+            assert _close(v, want, scale), (name, v, want, scale)
+        for M, v in zip(small, vals[len(big):]):
+            want, scale = oracle.haf_formula(M, loops)
+            assert _close(v, want, scale), (M.shape[0], loops, v, want)
 
 
 def test_device_launch_matches_host_api():
@@ -357,8 +379,9 @@ def _launch_value(A, loops=False):
 
 def test_full_size_in_the_bench_configuration():
     """n = 48 in the configuration bench.py times (haf_launch, shipped launch
-    shape: an 8-warp launch and a 4-warp launch for the largest tiles):
-    haf(J_48) = 47!!, and a 24 + 24 block-diagonal matrix factorises."""
+    shape): haf(J_48) = 47!!, and a 24 + 24 block-diagonal matrix equals the
+    product of the oracle's hafnians of its two blocks (the block-diagonal
+    factorisation of Sec. 2)."""
     v, scale = _launch_value(np.ones((48, 48), dtype=complex))
     assert _close(v, oracle.double_factorial(47), scale)
     A = inputs.complex_gaussian_symmetric(24, 4801)
@@ -367,8 +390,8 @@ def test_full_size_in_the_bench_configuration():
     M[:24, :24] = A
     M[24:, 24:] = C
     v, scale = _launch_value(M)
-    a, c = hg.haf_info(A), hg.haf_info(C)
-    assert _close(v, a.value * c.value, scale)
+    (a, sa), (c, sc) = oracle.haf_formula(A), oracle.haf_formula(C)
+    assert _close(v, a * c, scale), (v, a * c, scale)
 
 
 def test_bitwise_reproducible():

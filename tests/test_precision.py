@@ -13,6 +13,8 @@ import oracle
 import paper_1805_12498_gb300 as hg
 from paper_1805_12498_gb300 import inputs
 
+from golden import cases as golden_cases
+
 pytestmark = pytest.mark.gpu
 
 TOL32 = hg.HAF_FP32_REL_TOL
@@ -59,8 +61,7 @@ def test_fp32_against_stored_oracle_sums():
     with open(path) as f:
         cases = json.load(f)["cases"]
     for c in cases:
-        A = (inputs.real_gaussian_symmetric(c["n"], c["seed"]) if c["real"]
-             else inputs.complex_gaussian_symmetric(c["n"], c["seed"]))
+        A = golden_cases.case_matrix(c)
         got = hg.haf_info(A, loops=c["loops"], real=c["real"], precision="fp32")
         want = complex(c["re"], c["im"])
         assert abs(got.value - want) <= TOL32 * c["abs_sum"], (c["name"], got.value, want, c["abs_sum"])
