@@ -46,8 +46,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) of one launch of the dominant subset kernel at
-# n = 48, from the ncu capture in profiles/subset_kernel_complex_n48_dram.md;
-# re-capture when the kernel changes.
+# n = 48, from the one-pass ncu capture of this workload kept under
+# profiles/; re-captured whenever the kernel changes.
 TRAFFIC_BYTES = {48: 1645568 + 0}
 
 
@@ -62,6 +62,15 @@ def alg_flops(n: int) -> float:
     (44/3) sum_m C(h,m) (2m)^3 = (44/3) 2^h h^2 (h+3)."""
     h = n // 2
     return (44.0 / 3.0) * (2 ** h) * h * h * (h + 3)
+
+
+def alg_flops_lhaf(n: int) -> float:
+    """Algorithmic FP64 flops of one loop hafnian: the hafnian's count plus,
+    per subset, the loop moments' 8 ((h-1) N^2 / 2 + 2 N^2) (N = 2|Z|)."""
+    from math import comb
+    h = n // 2
+    extra = sum(comb(h, m) * 8.0 * ((h - 1) * (2 * m) ** 2 / 2.0 + 2.0 * (2 * m) ** 2) for m in range(1, h + 1))
+    return alg_flops(n) + extra
 
 
 class ClockSampler:
@@ -170,17 +179,25 @@ def batched_leg(count: int, seed: int, reps: int = 3):
 
 
 def precision_leg(seed: int, value48=None):
-    """Precision study: FP32-bulk mode against FP64 at n = 40
-    and 48 on a complex Gaussian matrix and on a GBS submatrix (haf).  Errors
-    of the values are relative to abs_sum = sum_Z |f(Z)| (the stated form) and
-    to |haf|; sampled summands of the two modes against each other (the
-    tests pin both to the binary128 oracle)."""
+    """Precision study: FP32-bulk mode against FP64 at n = 16, 40 and 48 on a
+    complex Gaussian matrix and on a GBS submatrix (haf).  Errors of the
+    values relative to abs_sum = sum_Z |f(Z)| (the stated per-unit error) and
+    to |haf|; the accuracy gate's decision (admitted when the estimate
+    HAF_FP32_REL_TOL * abs_sum / |value| <= HAF_FP32_MAX_REL_ERR, else
+    refused with HAF_EACCURACY); sampled summands of the two modes against
+    each other (the tests pin both to the binary128 oracle)."""
     import paper_1805_12498_gb300 as hg
     from paper_1805_12498_gb300 import inputs
 
+    def fp32(A):
+        try:
+            return hg.haf_info(A, precision="fp32"), True
+        except hg.HafAccuracyError as e:
+            return e.result, False
+
     rows = []
     for kind in ("gauss", "gbs"):
-        for n in (40, 48):
+        for n in (16, 40, 48):
             if kind == "gauss":
                 A = inputs.complex_gaussian_symmetric(n, seed if n == 48 else seed + n)
             else:
@@ -192,9 +209,9 @@ def precision_leg(seed: int, value48=None):
                 t = time.perf_counter()
                 r = hg.haf_info(A)
                 v64, a64, t64 = r.value, r.abs_sum, time.perf_counter() - t
-            hg.haf_info(A, precision="fp32")
+            fp32(A)
             t = time.perf_counter()
-            r32 = hg.haf_info(A, precision="fp32")
+            r32, admitted = fp32(A)
             t32 = time.perf_counter() - t
             d = abs(r32.value - v64)
             masks = inputs.random_masks(n // 2, 1024, seed=seed + n)
@@ -202,11 +219,13 @@ def precision_leg(seed: int, value48=None):
             rel = np.abs(hg.haf_terms(A, masks, precision="fp32") - f64) / np.abs(f64)
             rows.append({"input": kind, "n": n, "err_over_abs_sum": d / a64,
                          "err_over_abs_value": d / max(abs(v64), 1e-300), "abs_value_over_abs_sum": abs(v64) / a64,
+                         "rel_err_bound": r32.rel_err_bound, "admitted": admitted,
                          "s_fp64": t64, "s_fp32": t32, "speedup": t64 / t32,
                          "term_rel_err_median": float(np.median(rel)), "term_rel_err_max": float(rel.max())})
-    return {"workload": "haf, n = 40 and 48, complex Gaussian symmetric and GBS submatrix of a 32-mode kernel (r = 0.88); "
-                        "FP32 bulk (single-precision Householder + La Budde) vs FP64; 1024 sampled summands per case",
-            "stated_tol_over_abs_sum": hg.HAF_FP32_REL_TOL, "rows": rows}
+    return {"workload": "haf, n = 16, 40 and 48, complex Gaussian symmetric and GBS submatrix of a 32-mode kernel "
+                        "(r = 0.88); FP32 bulk (single-precision Householder + La Budde) vs FP64; 1024 sampled "
+                        "summands per case",
+            "stated_tol_over_abs_sum": hg.HAF_FP32_REL_TOL, "max_rel_err": hg.HAF_FP32_MAX_REL_ERR, "rows": rows}
 
 
 def lowrank_leg(seed: int):
@@ -348,6 +367,113 @@ def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
             "max_ms": float(lat.max())}
 
 
+def lhaf_leg(hg, torch, dA, n, stream, flush, steps: int, peak: float):
+    """Loop hafnian of the same matrix (its diagonal kept), device-resident
+    and CUDA-event timed on the launching stream like the headline (L2 flushed
+    between steps); roofline against the lhaf algorithmic flop count."""
+    dev = dA.device
+    ws = hg.workspace_bytes(n, loops=True)
+    work = torch.empty(ws // 8 + 64, dtype=torch.float64, device=dev)
+    wptr = (work.data_ptr() + 255) // 256 * 256
+    out = torch.zeros(5, dtype=torch.float64, device=dev)
+
+    def step():
+        hg.haf_launch(dA.data_ptr(), n, out.data_ptr(), wptr, ws, stream.cuda_stream, loops=True)
+
+    step()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    achieved = alg_flops_lhaf(n) / (ms * 1e-3) / 1e12
+    return {"workload": f"lhaf of the same {n}x{n} matrix (diagonal kept), 2^{n // 2} subset terms",
+            "ms_per_step": ms, "steps": steps, "subset_terms_per_s": 2 ** (n // 2) / (ms * 1e-3),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "note": "haf flops + per subset 8 ((h-1) N^2/2 + 2 N^2) for the loop moments; "
+                                 "CUDA-event time; peak = DFMA probe (of measured)"}}
+
+
+def summary_fields(line: dict) -> dict:
+    """Short top-level scalars of the side legs, so that a record that keeps
+    only the line's first keys still has them."""
+    out = {}
+    if "lhaf" in line:
+        out["lhaf_ms_per_step"] = line["lhaf"]["ms_per_step"]
+        out["lhaf_over_haf"] = line["lhaf"]["ms_per_step"] / line["ms_per_step"]
+        out["lhaf_roofline_frac"] = line["lhaf"]["roofline"]["frac"]
+    if "batched" in line:
+        out["batched_haf_per_s"] = line["batched"]["haf_per_s"]
+        out["batched_speedup_vs_one_launch_per_haf"] = line["batched"]["speedup_vs_one_launch_per_haf"]
+    if "serving" in line:
+        sv = line["serving"]
+        out["serving_capacity_vs_one_launch"] = sv["capacity_vs_one_launch"]
+        out["serving_p50_ms"] = sv["p50_ms"]
+        out["serving_p99_ms"] = sv["p99_ms"]
+        out["one_launch_fifo_p50_ms"] = sv["one_launch_fifo_p50_ms"]
+        out["one_launch_fifo_p99_ms"] = sv["one_launch_fifo_p99_ms"]
+    return out
+
+
+def run_shard(args, hg, inputs, torch, dist, world: int, rank: int, dev):
+    """One hafnian split over the ranks: rank p evaluates part p of `world`
+    of every size class of the subset sum (haf_part, host pointers), the
+    40-byte part records are gathered and combined in part order on rank 0
+    (haf_combine).  Strong scaling: the work per step is one hafnian."""
+    n, h = args.n, args.n // 2
+    A = inputs.complex_gaussian_symmetric(n, args.seed)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(1, args.warmup)):
+        hg.haf_part(A, rank, world)
+    times, value, abs_sum = [], None, None
+    for _ in range(args.steps):
+        barrier()
+        t0 = time.perf_counter()
+        rec = hg.haf_part(A, rank, world)
+        t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+        recs = torch.tensor(rec, dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            gathered = [torch.zeros_like(recs) for _ in range(world)]
+            dist.all_gather(gathered, recs)
+            allrec = torch.stack(gathered).cpu().numpy()
+        else:
+            allrec = recs.cpu().numpy()[None, :]
+        value, abs_sum = hg.combine(allrec)
+        times.append(float(t[0]))
+    barrier()
+    s_step = statistics.mean(times)
+    if rank == 0:
+        achieved = alg_flops(n) / s_step / 1e12
+        peak, _ = hg.fp64_peak()
+        line = {"metric": f"subset-terms/s (one haf sharded over ranks, n={n}, complex128)",
+                "value": 2 ** h / s_step, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": s_step * 1e3, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f64 (complex128, double-double subset sum)", "data": "synthetic",
+                "config": {"workload": f"haf of one seeded complex Gaussian symmetric {n}x{n} matrix split into "
+                                       f"{world} subset-range parts (one per rank), part records combined on rank 0",
+                           "n": n, "l2": "inputs far below L2; each step is seconds of FP64 work",
+                           "parallelism": f"subset-range shards x{world}"},
+                "result": {"re": value.real, "im": value.imag, "abs_sum": abs_sum},
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak / world,
+                             "note": "per-GPU fraction: (44/3) 2^h h^2 (h+3) flops / (host-clock step time x ranks); "
+                                     "peak = DFMA probe of rank 0 (of measured)"},
+                "e2e": {"value": 2 ** h / s_step, "unit": UNIT, "h2d_bytes_per_step": world * n * n * 16,
+                        "d2h_bytes_per_step": world * 40},
+                "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -383,6 +509,9 @@ def main():
                     help="requests in the serving leg (0 skips it)")
     ap.add_argument("--serve-nmax", type=int, default=40)
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32-vs-FP64 precision leg")
+    ap.add_argument("--no-lhaf", action="store_true", help="skip the loop-hafnian leg")
+    ap.add_argument("--shard", action="store_true",
+                    help="split ONE hafnian of size --n over the ranks (strong scaling) instead of one per rank")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -400,6 +529,12 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
+
+    if args.shard:
+        run_shard(args, hg, inputs, torch, dist, world, rank, dev)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     n, h = args.n, args.n // 2
     A = inputs.complex_gaussian_symmetric(n, args.seed + rank)
@@ -489,6 +624,8 @@ def main():
         }
         # the single-GPU legs run at N = 1 only (a scaling run reports the
         # headline metric alone)
+        if not args.no_lhaf and world == 1:
+            line["lhaf"] = lhaf_leg(hg, torch, dA, n, stream, flush, max(2, min(args.steps, 5)), peak_tflops)
         if args.gbs_batch > 0 and world == 1:
             line["batched"] = batched_leg(args.gbs_batch, args.seed)
         if args.serve_requests > 0 and world == 1:
@@ -499,7 +636,14 @@ def main():
                                                           ms_step * 1e-3))
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(n, args.seed)
+        summary = summary_fields(line)
+        # scalars first, after the contract's keys; the large leg objects last
+        legs = {k: line.pop(k) for k in ("lhaf", "batched", "serving", "lowrank", "precision") if k in line}
+        line.update(summary)
+        line.update(legs)
         print(json.dumps(line), flush=True)
+        sys.stderr.write("summary: " + json.dumps({"value": value, "ms_per_step": ms_step,
+                                                   "roofline_frac": line["roofline"]["frac"], **summary}) + "\n")
     if world > 1:
         dist.destroy_process_group()
 

@@ -38,8 +38,10 @@
  * tests is |error| <= 1e-10 * abs_sum).
  *
  * Errors.  Every entry point returns HAF_OK (0) or a negative HAF_E* code
- * and never throws across the ABI.  On error the outputs are left untouched.
- * haf_last_error() returns a short text for the calling thread's last error.
+ * and never throws across the ABI.  On error the outputs are left untouched,
+ * except for HAF_EACCURACY (FP32-bulk mode, below), which writes the value
+ * and the report so that the caller can inspect them.  haf_last_error()
+ * returns a short text for the calling thread's last error.
  */
 #ifndef HAFNIAN_GB300_H
 #define HAFNIAN_GB300_H
@@ -62,31 +64,52 @@ extern "C" {
 #define HAF_EBUSY (-5)     /* server refused a job (queue full)                    */
 #define HAF_ENOTFOUND (-6) /* server: unknown (or already collected) ticket        */
 #define HAF_ESMALL (-7)    /* caller-supplied workspace too small                  */
+#define HAF_EACCURACY (-8) /* FP32-bulk result above the stated relative error      */
 
 /* flags */
 #define HAF_FLAG_LOOPS (1u << 0) /* loop hafnian                                 */
 #define HAF_FLAG_REAL (1u << 1)  /* A is real float64, not complex128           */
 #define HAF_FLAG_FP32 (1u << 2)  /* FP32-bulk precision mode (see below)         */
 
-/* FP32-bulk precision mode.  With HAF_FLAG_FP32 the gather of B, the
+/* Accuracy.  The signed subset sum cancels: |value| is often many orders
+ * of magnitude below abs_sum = sum_Z |f(Z)|, so an error that is small
+ * against abs_sum can be large against the value.  Each whole-matrix call
+ * therefore reports rel_err_bound = REL_TOL * abs_sum / |value|, an
+ * estimate of |error| / |value| from the measured error against the
+ * binary128 oracle, where REL_TOL is
+ *   HAF_FP64_REL_TOL for FP64 (measured errors up to 1.2e-14 * abs_sum), or
+ *   HAF_FP32_REL_TOL for the FP32-bulk mode.
+ *
+ * FP32-bulk precision mode.  With HAF_FLAG_FP32 the gather of B, the
  * Householder reduction, the loop moments and La Budde's recurrence run in
  * single precision (complex64 / float32) while the power series, f(Z) and
- * the double-double subset sum stay FP64.  Its error against the FP64
- * oracle is measured, not bounded a priori; the mode is offered only for
- * n <= HAF_FP32_MAX_N, the sizes at which the measured error stayed within
- * HAF_FP32_REL_TOL * abs_sum (abs_sum = sum_Z |f(Z)|).  Calls with larger n
- * return HAF_EINVAL.  Whether that is accurate enough for a given use
- * depends on |haf| / abs_sum, which the library reports with each value. */
+ * the double-double subset sum stay FP64 (Sec. 4 finds that the precision of
+ * the eigenvalue step dominates the error; this mode trades it for speed).
+ * Its error is bounded in practice by HAF_FP32_REL_TOL * abs_sum.  A
+ * whole-matrix call in this mode is gated on the value: when rel_err_bound
+ * exceeds HAF_FP32_MAX_REL_ERR it returns HAF_EACCURACY (the value and the
+ * report are still written; recompute without HAF_FLAG_FP32 for a result in
+ * FP64).  Inputs with heavy cancellation -- random Gaussian or GBS matrices
+ * beyond n of about 16 -- are refused; inputs with little cancellation are
+ * admitted at any n <= HAF_FP32_MAX_N.  The device-pointer form haf_launch
+ * and the part records of haf_part are not gated (their value is on the
+ * device, or is only a part of the sum). */
 #define HAF_FP32_MAX_N 56
-#define HAF_FP32_REL_TOL 1e-4
+#define HAF_FP64_REL_TOL 1e-13
+#define HAF_FP32_REL_TOL 2e-6
+#define HAF_FP32_MAX_REL_ERR 1e-3
 
 /* Per-call report. */
 typedef struct haf_info {
-  double abs_sum;     /* sum over subsets Z of |f(Z)|                          */
-  double value_lo[2]; /* low parts of the double-double result (re, im)        */
-  int64_t subsets;    /* number of subset terms evaluated (2^{n/2} - 1)        */
-  double seconds;     /* wall time of the call (host clock)                    */
-  int64_t launches;   /* CUDA kernels launched by the call                     */
+  double abs_sum;        /* sum over subsets Z of |f(Z)|                       */
+  double value_lo[2];    /* low parts of the double-double result (re, im)     */
+  int64_t subsets;       /* number of subset terms evaluated (2^{n/2} - 1)     */
+  double seconds;        /* wall time of the call (host clock)                 */
+  int64_t launches;      /* CUDA kernels launched by the call                  */
+  double rel_err_bound;  /* estimated |error| / |value| (see Accuracy); 0 where
+                            not computed (parts, the low-rank path)            */
+  int32_t precision_mode; /* 0: FP64, 1: FP32-bulk                             */
+  int32_t reserved;
 } haf_info;
 
 /* ------------------------------------------------------------------------

@@ -21,15 +21,21 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _native, tuning
-from ._native import HAF_FLAG_FP32, HAF_FLAG_LOOPS, HAF_FLAG_REAL, HAF_MAX_N, HafError  # noqa: F401
+from ._native import (HAF_FLAG_FP32, HAF_FLAG_LOOPS, HAF_FLAG_REAL, HAF_MAX_N, HafAccuracyError,  # noqa: F401
+                      HafError)
 
 __all__ = ["haf", "lhaf", "haf_info", "haf_batched", "haf_terms", "workspace_bytes",
            "haf_launch", "haf_launch_noalloc", "haf_part", "part_subsets", "combine", "Server", "fp64_peak", "tune",
-           "tune_set", "batched_tune", "haf_lowrank", "HafError", "HAF_MAX_N", "HAF_FP32_MAX_N", "HAF_FP32_REL_TOL"]
+           "tune_set", "batched_tune", "haf_lowrank", "HafError", "HafAccuracyError", "HAF_MAX_N",
+           "HAF_FP32_MAX_N", "HAF_FP32_REL_TOL", "HAF_FP64_REL_TOL", "HAF_FP32_MAX_REL_ERR"]
 
-# FP32-bulk mode: offered for n <= HAF_FP32_MAX_N (include/hafnian_gb300.h)
+# Accuracy constants of include/hafnian_gb300.h: the error per unit of
+# abs_sum measured against the oracle (FP64, FP32-bulk) and the bound on the
+# estimated relative error above which an FP32-bulk result is refused.
 HAF_FP32_MAX_N = 56
-HAF_FP32_REL_TOL = 1e-4
+HAF_FP64_REL_TOL = 1e-13
+HAF_FP32_REL_TOL = 2e-6
+HAF_FP32_MAX_REL_ERR = 1e-3
 
 
 def _flags(loops: bool = False, real: bool = False, precision: str = "fp64") -> int:
@@ -47,6 +53,13 @@ class Info:
     subsets: int
     seconds: float
     launches: int
+    rel_err_bound: float = 0.0  # estimated |error| / |value| (0: not computed)
+    precision_mode: int = 0     # 0: FP64, 1: FP32-bulk
+
+
+def _info(value, info) -> Info:
+    return Info(value, info.abs_sum, complex(info.value_lo[0], info.value_lo[1]), info.subsets, info.seconds,
+                info.launches, info.rel_err_bound, info.precision_mode)
 
 
 def _prep(A, real: bool) -> np.ndarray:
@@ -68,14 +81,17 @@ def haf_info(A, loops: bool = False, real: bool | None = None, precision: str = 
     if precision == "fp64":
         fn = {(False, False): L.haf_c128, (True, False): L.lhaf_c128,
               (False, True): L.haf_f64, (True, True): L.lhaf_f64}[(bool(loops), bool(real))]
-        _native.check(fn(A.ctypes.data_as(_native._DP), A.shape[0], out.ctypes.data_as(_native._DP),
-                         ctypes.byref(info)))
+        rc = fn(A.ctypes.data_as(_native._DP), A.shape[0], out.ctypes.data_as(_native._DP), ctypes.byref(info))
     else:
-        _native.check(L.haf_eval(A.ctypes.data_as(_native._DP), A.shape[0], _flags(loops, real, precision),
-                                 out.ctypes.data_as(_native._DP), ctypes.byref(info)))
-    val = complex(out[0], 0.0 if real else out[1])
-    return Info(val, info.abs_sum, complex(info.value_lo[0], info.value_lo[1]), info.subsets,
-                info.seconds, info.launches)
+        rc = L.haf_eval(A.ctypes.data_as(_native._DP), A.shape[0], _flags(loops, real, precision),
+                        out.ctypes.data_as(_native._DP), ctypes.byref(info))
+    result = _info(complex(out[0], 0.0 if real else out[1]), info)
+    try:
+        _native.check(rc)
+    except HafAccuracyError as e:
+        e.result = result  # the refused FP32-bulk value and its report
+        raise
+    return result
 
 
 def haf(A, loops: bool = False, precision: str = "fp64"):
@@ -104,13 +120,18 @@ def haf_batched(mats, loops: bool = False, with_info: bool = False, precision: s
     outs = np.zeros(2 * max(1, count))
     infos = (_native.HafInfo * max(1, count))()
     L = _native.lib()
-    _native.check(L.haf_batched(ptrs, ns.ctypes.data_as(_native._I64P), count, _flags(loops, False, precision),
-                                outs.ctypes.data_as(_native._DP), infos))
+    rc = L.haf_batched(ptrs, ns.ctypes.data_as(_native._I64P), count, _flags(loops, False, precision),
+                       outs.ctypes.data_as(_native._DP), infos)
     vals = outs[0:2 * count:2] + 1j * outs[1:2 * count:2]
+    result = [_info(complex(vals[i]), infos[i]) for i in range(count)]
+    try:
+        _native.check(rc)
+    except HafAccuracyError as e:
+        e.result = (vals, result)
+        raise
     if not with_info:
         return vals
-    return vals, [Info(complex(vals[i]), infos[i].abs_sum, complex(*infos[i].value_lo), infos[i].subsets,
-                       infos[i].seconds, infos[i].launches) for i in range(count)]
+    return vals, result
 
 
 def haf_terms(A, masks, loops: bool = False, precision: str = "fp64") -> np.ndarray:
@@ -217,8 +238,7 @@ class Server:
         us = -1 if timeout_s is None else int(timeout_s * 1e6)
         _native.check(self._L.haf_server_poll(self._h, ticket, out.ctypes.data_as(_native._DP),
                                                ctypes.byref(info), us))
-        return Info(complex(out[0], out[1]), info.abs_sum, complex(info.value_lo[0], info.value_lo[1]),
-                    info.subsets, info.seconds, info.launches)
+        return _info(complex(out[0], out[1]), info)
 
     def close(self) -> None:
         if self._h:
@@ -250,8 +270,7 @@ def haf_lowrank(G) -> Info:
     info = _native.HafInfo()
     _native.check(_native.lib().haf_lowrank_c128(G.ctypes.data_as(_native._DP), G.shape[0], G.shape[1],
                                                  out.ctypes.data_as(_native._DP), ctypes.byref(info)))
-    return Info(complex(out[0], out[1]), info.abs_sum, complex(info.value_lo[0], info.value_lo[1]), info.subsets,
-                info.seconds, info.launches)
+    return _info(complex(out[0], out[1]), info)
 
 
 def tune(n: int, loops: bool = False, real: bool = False, precision: str = "fp64", reps: int = 1) -> dict:

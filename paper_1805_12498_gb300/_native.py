@@ -21,6 +21,7 @@ HAF_ETIMEDOUT = -4
 HAF_EBUSY = -5
 HAF_ENOTFOUND = -6
 HAF_ESMALL = -7
+HAF_EACCURACY = -8
 HAF_FLAG_LOOPS = 1
 HAF_FLAG_REAL = 2
 HAF_FLAG_FP32 = 4
@@ -30,7 +31,8 @@ HAF_MAX_N = 56
 class HafInfo(ctypes.Structure):
     _fields_ = [("abs_sum", ctypes.c_double), ("value_lo", ctypes.c_double * 2),
                 ("subsets", ctypes.c_int64), ("seconds", ctypes.c_double),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("rel_err_bound", ctypes.c_double),
+                ("precision_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -47,6 +49,13 @@ class HafError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"hafnian_gb300 error {code}: {msg}")
         self.code = code
+
+
+class HafAccuracyError(HafError):
+    """An FP32-bulk result whose estimated relative error exceeds
+    HAF_FP32_MAX_REL_ERR (HAF_EACCURACY).  ``result`` holds the value and
+    report the library wrote anyway (set by the caller that raises it)."""
+    result = None
 
 
 _lib = None
@@ -140,4 +149,5 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
 def check(rc: int) -> None:
     if rc != HAF_OK:
         msg = lib().haf_last_error()
-        raise HafError(rc, msg.decode() if msg else "")
+        cls = HafAccuracyError if rc == HAF_EACCURACY else HafError
+        raise cls(rc, msg.decode() if msg else "")

@@ -80,14 +80,16 @@ struct SizeCfg {
 };
 
 // Smallest lane-group width whose S = 32/G subsets fit the warp slice
-// (kernel kind `kind`, `warp_bytes` of shared memory per warp).
-bool choose_cfg(int N, int h, int kind, int warp_bytes, SizeCfg* out) {
+// (kernel kind `kind`, `warp_bytes` of shared memory per warp); at equal
+// width an odd leading dimension (column walks on distinct banks) is
+// preferred to ld = N.
+bool choose_cfg(int N, int h, int kind, int loops, int warp_bytes, SizeCfg* out) {
   const int sb = bulk_elem_bytes(kind), ss = series_elem_bytes(kind);
   const bool mixed = kind_mixed(kind);
-  for (int ld : {N + 1, N}) {
-    for (int G = 1; G <= 32; G *= 2) {
+  for (int G = 1; G <= 32; G *= 2) {
+    for (int ld : {N + 1, N}) {
       const int S = 32 / G;
-      if ((long)S * subset_bytes(N, ld, h, sb, ss, mixed) <= warp_bytes) {
+      if ((long)S * subset_bytes(N, ld, h, sb, ss, mixed, loops != 0) <= warp_bytes) {
         out->G = G;
         out->ld = ld;
         return true;
@@ -136,7 +138,7 @@ int build_plan(const std::vector<JobSpec>& jobs, int sms, const PlanCfg& pc, Pla
       c.job = (int)jb;
       c.m = m;
       c.wpb = pc.wpb;
-      while (!choose_cfg(2 * m, h, kind, warp_bytes_for(c.wpb), &c.cfg)) {
+      while (!choose_cfg(2 * m, h, kind, js.loops, warp_bytes_for(c.wpb), &c.cfg)) {
         if (c.wpb == 4) return fail(HAF_EINVAL, "matrix too large for the shared-memory plan");
         c.wpb /= 2;
       }
@@ -398,6 +400,28 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Estimated |error| / |value| of a whole-matrix result (the Accuracy
+// paragraph of the header): the measured error per unit of abs_sum, scaled
+// by abs_sum / |value|.
+double rel_err_bound(double re, double im, double abs_sum, int prec) {
+  const double tol = prec == kPrecF32 ? HAF_FP32_REL_TOL : HAF_FP64_REL_TOL;
+  const double v = std::hypot(re, im);
+  if (abs_sum == 0.0) return 0.0;
+  if (v == 0.0) return HUGE_VAL;
+  return tol * abs_sum / v;
+}
+
+// The FP32-bulk gate: HAF_EACCURACY when the estimated relative error of an
+// FP32-bulk result exceeds HAF_FP32_MAX_REL_ERR.
+int accuracy_gate(double rel, int prec, const char* where) {
+  if (prec != kPrecF32 || rel <= HAF_FP32_MAX_REL_ERR) return HAF_OK;
+  char msg[200];
+  std::snprintf(msg, sizeof(msg),
+                "%s: FP32-bulk result's estimated relative error %.3g exceeds HAF_FP32_MAX_REL_ERR (%.0e); "
+                "recompute in FP64", where, rel, (double)HAF_FP32_MAX_REL_ERR);
+  return fail(HAF_EACCURACY, msg);
+}
+
 // Synchronous single matrix from host memory.
 int run_single(const double* A, int64_t n64, int loops, int is_real, int prec, double* out, haf_info* info) {
   const double t0 = now_s();
@@ -406,10 +430,12 @@ int run_single(const double* A, int64_t n64, int loops, int is_real, int prec, d
   if (!out || (n64 > 0 && !A)) return fail(HAF_EINVAL, "null pointer");
   int n = (int)n64;
   const int elem = is_real ? 1 : 2;
+  double rel = 0.0;
   auto write = [&](double re, double im, double lre, double lim, double abs_sum, int64_t subsets,
                    int64_t launches) {
     out[0] = re;
     if (!is_real) out[1] = im;
+    rel = rel_err_bound(re, is_real ? 0.0 : im, abs_sum, prec);
     if (info) {
       info->abs_sum = abs_sum;
       info->value_lo[0] = lre;
@@ -417,6 +443,9 @@ int run_single(const double* A, int64_t n64, int loops, int is_real, int prec, d
       info->subsets = subsets;
       info->seconds = now_s() - t0;
       info->launches = launches;
+      info->rel_err_bound = rel;
+      info->precision_mode = prec == kPrecF32 ? 1 : 0;
+      info->reserved = 0;
     }
   };
   if (n == 0) {
@@ -470,7 +499,7 @@ int run_single(const double* A, int64_t n64, int loops, int is_real, int prec, d
   HAF_CUDA(cudaStreamSynchronize(st));
   const double* o = d->host_out;
   write(o[0] + o[2], o[1] + o[3], o[2], o[3], o[4], dp->subsets, 2 + (int64_t)dp->segs.size());
-  return HAF_OK;
+  return accuracy_gate(rel, prec, "haf_eval");
 }
 
 // Part `part` of `nparts` of the subset sum of one matrix (host pointers,
@@ -490,7 +519,7 @@ int run_part(const double* A, int64_t n64, int loops, int is_real, int prec, int
     rec[0] = (part == 0) ? v : 0.0;
     rec[1] = rec[2] = rec[3] = 0.0;
     rec[4] = (part == 0) ? std::fabs(v) : 0.0;
-    if (info) *info = haf_info{rec[4], {0.0, 0.0}, 0, now_s() - t0, 0};
+    if (info) *info = haf_info{rec[4], {0.0, 0.0}, 0, now_s() - t0, 0, 0.0, prec == kPrecF32 ? 1 : 0, 0};
     return HAF_OK;
   };
   if (n == 0) return trivial(1.0);
@@ -538,7 +567,9 @@ int run_part(const double* A, int64_t n64, int loops, int is_real, int prec, int
     HAF_CUDA(cudaStreamSynchronize(st));
     std::memcpy(rec, d->host_out, 5 * sizeof(double));
   }
-  if (info) *info = haf_info{rec[4], {rec[2], rec[3]}, dp->subsets, now_s() - t0, dp->nchunks ? 2 + (int64_t)dp->segs.size() : 1};
+  if (info)
+    *info = haf_info{rec[4], {rec[2], rec[3]}, dp->subsets, now_s() - t0, dp->nchunks ? 2 + (int64_t)dp->segs.size() : 1,
+                     0.0, prec == kPrecF32 ? 1 : 0, 0};
   return HAF_OK;
 }
 
@@ -719,7 +750,7 @@ int batch_sizes(const double* const* As, const int64_t* ns, int64_t count, int l
         outs[2 * b] = v;
         outs[2 * b + 1] = 0.0;
       }
-      if (infos) infos[b] = haf_info{v, {0.0, 0.0}, 0, 0.0, 0};
+      if (infos) infos[b] = haf_info{v, {0.0, 0.0}, 0, 0.0, 0, 0.0, prec == kPrecF32 ? 1 : 0, 0};
       continue;
     }
     if (n + (n & 1) > kMaxN) return fail(HAF_EINVAL, "n out of range");
@@ -774,15 +805,28 @@ int run_batched(const double* const* As, const int64_t* ns, int64_t count, int l
   HAF_CUDA(cudaGraphLaunch(bp.exec, d->stream));
   HAF_CUDA(cudaStreamSynchronize(d->stream));
   const double secs = now_s() - t0;
+  double worst = 0.0;
+  int64_t worst_b = -1;
   for (size_t j = 0; j < sizes.size(); ++j) {
     const double* o = bp.h_out + 5 * j;
     const int64_t b = idx[j];
     outs[2 * b] = o[0] + o[2];
     outs[2 * b + 1] = o[1] + o[3];
+    const double rel = rel_err_bound(o[0] + o[2], o[1] + o[3], o[4], prec);
+    if (rel > worst || worst_b < 0) {
+      worst = rel;
+      worst_b = b;
+    }
     if (infos) {
       const int h = sizes[j] / 2;
-      infos[b] = haf_info{o[4], {o[2], o[3]}, (int64_t)((1ull << h) - 1), secs, 2 + (int64_t)bp.nsegs};
+      infos[b] = haf_info{o[4], {o[2], o[3]}, (int64_t)((1ull << h) - 1), secs, 2 + (int64_t)bp.nsegs,
+                          rel, prec == kPrecF32 ? 1 : 0, 0};
     }
+  }
+  if (prec == kPrecF32 && worst > HAF_FP32_MAX_REL_ERR) {
+    char where[64];
+    std::snprintf(where, sizeof(where), "haf_batched (matrix %lld)", (long long)worst_b);
+    return accuracy_gate(worst, prec, where);
   }
   return HAF_OK;
 }
@@ -980,7 +1024,7 @@ int haf_terms(const double* A, int64_t n64, uint32_t flags, const uint64_t* mask
     }
     int wpb = pc.wpb;
     SizeCfg cfg;
-    while (!choose_cfg(2 * m, h, kind, warp_bytes_for(wpb), &cfg)) {
+    while (!choose_cfg(2 * m, h, kind, loops, warp_bytes_for(wpb), &cfg)) {
       if (wpb == 4) return fail(HAF_EINVAL, "haf_terms: size too large");
       wpb /= 2;
     }
@@ -1335,7 +1379,7 @@ constexpr size_t kNoAllocBytes = HAF_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[HAF_NOALLOC_SCRATCH_BYTES];
 
 // Fixed layout inside the array.
-constexpr size_t kNaCounter = 0;
+constexpr size_t kNaCounter = 0;                                // 3 work counters
 constexpr size_t kNaTables = 256;                               // 256 doubles
 constexpr size_t kNaJobs = kNaTables + 256 * sizeof(double);    // one Job
 constexpr size_t kNaAt = kNaJobs + 256;                         // n*n*16 <= 56*56*16
@@ -1358,6 +1402,8 @@ NoAllocDevice g_na_dev[64];
 // Host-side plan storage (static: this path allocates nothing, host or device).
 Chunk g_na_chunks[kNaMaxChunks];
 int g_na_order[kNaMaxChunks];
+PlanSeg g_na_segs[3];
+int g_na_nsegs = 0;
 double g_na_tables[256];
 
 // Per-device set-up: the device address of the array (the host-side name
@@ -1369,6 +1415,10 @@ int noalloc_setup(int dev, NoAllocDevice** out) {
     void* ptr = nullptr;
     HAF_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
     HAF_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+    // with one chunk per warp every plan has at most sms * (16 + 8 + 4)
+    // chunks plus one partial chunk per size class and launch
+    if ((long)d.sms * 28 + 3 * (kMaxN / 2) > kNaMaxChunks)
+      return fail(HAF_EINVAL, "haf_launch_noalloc: the scratch array is too small for this GPU's SM count");
     HAF_CUDA(configure_kernels());
     for (int k = 0; k < 128; ++k) g_na_tables[k] = 0.5 * k;
     g_na_tables[128] = 0.0;
@@ -1380,46 +1430,67 @@ int noalloc_setup(int dev, NoAllocDevice** out) {
   return HAF_OK;
 }
 
-// Work plan for one matrix written into the static host arrays: sizes m = h
-// down to 1 (largest tiles first), each cut into chunks of roughly equal
-// work, at most kNaMaxChunks in total.  Returns the chunk count or < 0.
-int noalloc_plan(int n, int is_real, int num_warps) {
+// Work plan for one matrix written into the static host arrays, in the
+// launch shape `pc` (the one haf_launch uses for this n and kind): size
+// classes whose tiles do not fit pc.wpb warps per CTA drop to fewer; one
+// segment (launch) per warps-per-CTA value, most warps first, largest tiles
+// first inside each.  If the chunks exceed kNaMaxChunks the chunk
+// granularity is halved until they fit.  Returns the chunk count or < 0.
+int noalloc_plan(int n, int is_real, int loops, PlanCfg pc, int sms) {
   const int h = n / 2, kind = kernel_kind(is_real, kPrecF64);
-  double total = 0.0;
-  for (int m = 1; m <= h; ++m) total += (double)binom(h, m) * std::pow(2.0 * m, 3);
-  int per_warp = 8;
-  for (;;) {
-    const double target = std::max(1.0, total / (double)(num_warps * per_warp));
+  int wpb_of[kMaxN / 2 + 1];
+  SizeCfg cfg_of[kMaxN / 2 + 1];
+  double work[17] = {0};
+  for (int m = 1; m <= h; ++m) {
+    int w = pc.wpb;
+    while (!choose_cfg(2 * m, h, kind, loops, warp_bytes_for(w), &cfg_of[m])) {
+      if (w == 4) return fail(HAF_EINVAL, "haf_launch_noalloc: n too large");
+      w /= 2;
+    }
+    wpb_of[m] = w;
+    work[w] += (double)binom(h, m) * std::pow(2.0 * m, 3);
+  }
+  for (int per_warp = pc.chunks_per_warp;; per_warp = std::max(1, per_warp / 2)) {
     int nc = 0;
     bool over = false;
-    for (int m = h; m >= 1 && !over; --m) {
-      const int N = 2 * m;
-      SizeCfg cfg;
-      if (!choose_cfg(N, h, kind, kWarpBytes, &cfg)) return fail(HAF_EINVAL, "haf_launch_noalloc: n too large");
-      const int S = 32 / cfg.G;
-      const uint64_t cnt = binom(h, m);
-      uint64_t csz = (uint64_t)std::ceil(target / std::pow((double)N, 3) / S) * S;
-      csz = std::min<uint64_t>(std::max<uint64_t>(csz, (uint64_t)S), (uint64_t)1 << 30);
-      for (uint64_t r0 = 0; r0 < cnt; r0 += csz) {
-        if (nc >= kNaMaxChunks) {
-          over = true;
-          break;
+    g_na_nsegs = 0;
+    for (int w : {16, 8, 4}) {
+      const int begin = nc;
+      const double target = std::max(1.0, work[w] / ((double)sms * w * per_warp));
+      for (int m = h; m >= 1 && !over; --m) {
+        if (wpb_of[m] != w) continue;
+        const int N = 2 * m, S = 32 / cfg_of[m].G;
+        const uint64_t cnt = binom(h, m);
+        uint64_t csz = (uint64_t)std::ceil(target / std::pow((double)N, 3) / S) * S;
+        csz = std::min<uint64_t>(std::max<uint64_t>(csz, (uint64_t)S), (uint64_t)1 << 30);
+        for (uint64_t r0 = 0; r0 < cnt; r0 += csz) {
+          if (nc >= kNaMaxChunks) {
+            over = true;
+            break;
+          }
+          Chunk& c = g_na_chunks[nc];
+          std::memset(&c, 0, sizeof(c));
+          c.rank0 = r0;
+          c.mask0 = unrank_colex(r0, m, h);
+          c.count = (uint32_t)std::min<uint64_t>(csz, cnt - r0);
+          c.m = (uint8_t)m;
+          c.G = (uint8_t)cfg_of[m].G;
+          c.ld = (uint8_t)cfg_of[m].ld;
+          g_na_order[nc] = nc;
+          ++nc;
         }
-        Chunk& c = g_na_chunks[nc];
-        std::memset(&c, 0, sizeof(c));
-        c.rank0 = r0;
-        c.mask0 = unrank_colex(r0, m, h);
-        c.count = (uint32_t)std::min<uint64_t>(csz, cnt - r0);
-        c.m = (uint8_t)m;
-        c.G = (uint8_t)cfg.G;
-        c.ld = (uint8_t)cfg.ld;
-        g_na_order[nc] = nc;
-        ++nc;
+      }
+      if (over) break;
+      if (nc > begin) {
+        PlanSeg& sg = g_na_segs[g_na_nsegs++];
+        sg.begin = begin;
+        sg.end = nc;
+        sg.wpb = w;
+        sg.warp_bytes = warp_bytes_for(w);
       }
     }
     if (!over) return nc;
     if (per_warp == 1) return fail(HAF_EINVAL, "haf_launch_noalloc: plan exceeds the scratch array");
-    per_warp /= 2;
   }
 }
 
@@ -1431,13 +1502,25 @@ extern "C" int haf_launch_noalloc(const double* dA, int64_t n, uint32_t flags, d
   if (!dA || !d_out) return fail(HAF_EINVAL, "haf_launch_noalloc: null pointer");
   if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL)) return fail(HAF_EINVAL, "haf_launch_noalloc: unknown flags");
   const int loops = (flags & HAF_FLAG_LOOPS) ? 1 : 0, is_real = (flags & HAF_FLAG_REAL) ? 1 : 0;
-  std::lock_guard<std::mutex> lk(g_na_mu);
   int dev = 0;
   HAF_CUDA(cudaGetDevice(&dev));
+  // the launch shape haf_launch would use (tuned by haf_tune / haf_tune_set,
+  // else the default); a look-up only, nothing is created
+  PlanCfg pc;
+  pc.wpb = kWarpsPerBlock;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_devices.find(dev);
+    if (it != g_devices.end()) {
+      auto t = it->second->tuned.find(std::make_tuple((int)n, loops, is_real, (int)kPrecF64));
+      if (t != it->second->tuned.end()) pc = t->second;
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_na_mu);
   NoAllocDevice* d;
   int rc = noalloc_setup(dev, &d);
   if (rc) return rc;
-  const int nc = noalloc_plan((int)n, is_real, d->sms * kWarpsPerBlock);
+  const int nc = noalloc_plan((int)n, is_real, loops, pc, d->sms);
   if (nc < 0) return nc;
   cudaStream_t st = (cudaStream_t)stream;
   unsigned char* s = d->scratch;
@@ -1445,6 +1528,7 @@ extern "C" int haf_launch_noalloc(const double* dA, int64_t n, uint32_t flags, d
   int* order = (int*)(s + kNaChunks + (size_t)kNaMaxChunks * sizeof(Chunk));
   double* partials = (double*)(s + kNaChunks + (size_t)kNaMaxChunks * (sizeof(Chunk) + sizeof(int)));
   int* job_begin = (int*)(s + kNaJobBegin);
+  int* counters = (int*)(s + kNaCounter);  // one per launch
   const int jb[2] = {0, nc};
   double* At = (double*)(s + kNaAt);
   double* diag = (double*)(s + kNaDiag);
@@ -1454,21 +1538,24 @@ extern "C" int haf_launch_noalloc(const double* dA, int64_t n, uint32_t flags, d
   HAF_CUDA(cudaMemcpyAsync(job_begin, jb, sizeof(jb), cudaMemcpyHostToDevice, st));
   HAF_CUDA(cudaMemcpyAsync(chunks, g_na_chunks, (size_t)nc * sizeof(Chunk), cudaMemcpyHostToDevice, st));
   HAF_CUDA(cudaMemcpyAsync(order, g_na_order, (size_t)nc * sizeof(int), cudaMemcpyHostToDevice, st));
-  HAF_CUDA(cudaMemsetAsync(s + kNaCounter, 0, sizeof(int), st));
+  HAF_CUDA(cudaMemsetAsync(counters, 0, 3 * sizeof(int), st));
   HAF_CUDA(launch_prep(dA, (int)n, is_real, At, diag, st));
-  KernelArgs a;
-  a.jobs = (const Job*)(s + kNaJobs);
-  a.chunks = chunks;
-  a.order = order;
-  a.nchunks = nc;
-  a.counter = (int*)(s + kNaCounter);
-  a.partials = partials;
-  a.tables = (const double*)(s + kNaTables);
-  a.masks = nullptr;
-  a.terms_out = nullptr;
-  a.warp_bytes = kWarpBytes;
-  const int grid = std::max(1, std::min(d->sms, (nc + kWarpsPerBlock - 1) / kWarpsPerBlock));
-  HAF_CUDA(launch_subsets(a, kernel_kind(is_real, kPrecF64), kWarpsPerBlock, grid, st));
+  for (int si = 0; si < g_na_nsegs; ++si) {
+    const PlanSeg& sg = g_na_segs[si];
+    KernelArgs a;
+    a.jobs = (const Job*)(s + kNaJobs);
+    a.chunks = chunks;
+    a.order = order + sg.begin;
+    a.nchunks = sg.end - sg.begin;
+    a.counter = counters + si;
+    a.partials = partials;
+    a.tables = (const double*)(s + kNaTables);
+    a.masks = nullptr;
+    a.terms_out = nullptr;
+    a.warp_bytes = sg.warp_bytes;
+    const int grid = std::max(1, std::min(d->sms, (a.nchunks + sg.wpb - 1) / sg.wpb));
+    HAF_CUDA(launch_subsets(a, kernel_kind(is_real, kPrecF64), sg.wpb, grid, st));
+  }
   HAF_CUDA(launch_finalize(partials, job_begin, 1, d_out, st));
   return HAF_OK;
 }

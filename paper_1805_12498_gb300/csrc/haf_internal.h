@@ -114,19 +114,42 @@ inline int bulk_elem_bytes(int kind) {
 inline int series_elem_bytes(int kind) { return (kind & 1) ? 8 : 16; }
 inline bool kind_mixed(int kind) { return kind >= kKindC64; }
 
-// Shared-memory bytes of one subset.  Same-precision layout: tile N x ld,
-// five length-N vectors, six length-(h+1) series, h pair indices.  Mixed
-// layout: tile, five vectors and two length-(h+1) arrays in the bulk type
-// (subset_bulk_bytes, rounded to 16), then six length-(h+1) series in the
-// series type and the pair indices.
-inline __host__ __device__ int subset_bulk_bytes(int N, int ld, int h, int sb) {
-  const int b = (N * ld + 5 * N + 2 * (h + 1)) * sb;
-  return (b + 15) & ~15;
+// Shared-memory layout of one subset (byte offsets from the subset's base).
+// sb / ss: bytes of the bulk element (gather, Householder, loop moments, La
+// Budde) and of the series element (power series, f(Z)); equal in FP64.
+//   tile : N x ld bulk elements; after La Budde its first 4 (h+1) series
+//          elements hold the power-series arrays (GS, AC, ES, AC2), so it is
+//          at least that large
+//   vec  : W, P, TV (and VA, VB for the loop hafnian), N bulk elements each
+//   dnb  : La Budde's output, h+1 bulk elements (ub: loop moments, h+1)
+//   dn   : h+1 series elements (u: loop moments), equal to dnb / ub in FP64
+//   pos  : h ints, the pair list of the subset
+struct SubsetLayout {
+  int vec, dnb, ub, dn, u, pos, total;
+};
+inline __host__ __device__ int round16(int b) { return (b + 15) & ~15; }
+inline __host__ __device__ SubsetLayout subset_layout(int N, int ld, int h, int sb, int ss, bool mixed,
+                                                      bool loops) {
+  SubsetLayout L;
+  const int tile = N * ld * sb, ser = 4 * (h + 1) * ss;
+  L.vec = round16(tile > ser ? tile : ser);
+  L.dnb = L.vec + (loops ? 5 : 3) * N * sb;
+  L.ub = L.dnb + (h + 1) * sb;
+  int end = L.ub + (loops ? (h + 1) * sb : 0);
+  if (mixed) {
+    L.dn = round16(end);
+    L.u = L.dn + (h + 1) * ss;
+    end = L.u + (loops ? (h + 1) * ss : 0);
+  } else {
+    L.dn = L.dnb;
+    L.u = L.ub;
+  }
+  L.pos = round16(end);
+  L.total = round16(L.pos + 4 * h);
+  return L;
 }
-inline __host__ __device__ int subset_bytes(int N, int ld, int h, int sb, int ss, bool mixed) {
-  const int b = mixed ? subset_bulk_bytes(N, ld, h, sb) + 6 * (h + 1) * ss + 4 * h
-                      : (N * ld + 5 * N + 6 * (h + 1)) * sb + 4 * h;
-  return (b + 15) & ~15;
+inline __host__ __device__ int subset_bytes(int N, int ld, int h, int sb, int ss, bool mixed, bool loops) {
+  return subset_layout(N, ld, h, sb, ss, mixed, loops).total;
 }
 
 // Host planner (haf_capi.cu).

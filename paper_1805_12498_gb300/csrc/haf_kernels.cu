@@ -63,9 +63,27 @@ struct __align__(8) cplxf {
 template <class T>
 struct Ops;
 
+// Block sums over c lanes (defined below).
+template <class R>
+__device__ __forceinline__ R bsum1(R x, int c);
+template <class R>
+__device__ __forceinline__ void bsum2(R& x, R& y, int c);
+template <class R>
+__device__ __forceinline__ void bsum4(R& a, R& b, R& c2, R& d, int c);
+
+// x with its sign bit flipped when `neg` (an integer operation, not an
+// FP64 instruction).
+__device__ __forceinline__ double neg_if(double x, bool neg) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
+}
+__device__ __forceinline__ float neg_if(float x, bool neg) {
+  return __int_as_float(__float_as_int(x) ^ (neg ? (int)0x80000000u : 0));
+}
+
 template <>
 struct Ops<cplx> {
   using R = double;
+  static constexpr int kMadSlots = 4;  // FP64 instructions per multiply-add
   static __device__ __forceinline__ cplx zero() { return cplx{0.0, 0.0}; }
   static __device__ __forceinline__ cplx one() { return cplx{1.0, 0.0}; }
   // acc + a b
@@ -135,33 +153,47 @@ struct Ops<cplx> {
     return cplx{v.x, v.y};
   }
   static __device__ __forceinline__ cplx from_re(double x) { return cplx{x, 0.0}; }
+  // a, or conj(a) when `c`
+  static __device__ __forceinline__ cplx conj_sel(cplx a, bool c) { return cplx{a.re, neg_if(a.im, c)}; }
+  static __device__ __forceinline__ cplx block_sum(cplx a, int c) {
+    bsum2(a.re, a.im, c);
+    return a;
+  }
+  static __device__ __forceinline__ void block_sum2(cplx& a, cplx& b, int c) { bsum4(a.re, a.im, b.re, b.im, c); }
 
   // Householder vector for x = (x0, x1, ...), |x|^2 = nrm2, |x0|^2 = s0:
   // H = I - w w^H with w = c (x + e^{i arg x0} |x| e_1), c = 1/sqrt(|x|(|x|+|x0|)),
   // H x = alpha e_1 with alpha = -e^{i arg x0} |x| (Golub & Van Loan's sign
-  // choice, which avoids cancellation in the first entry).
+  // choice, which avoids cancellation in the first entry).  With the ratio
+  // r = |x| / |x0| = nrm2 / sqrt(nrm2 s0):
+  //   w_0 = c (1 + r) x0,  alpha = -r x0,  c = 1 / sqrt(nrm2 + s0 r),
+  // two reciprocal square roots (each costs several FP64 instructions).
+  // x0 = 0 takes the phase 1: r = |x|, w_0 = 1, alpha = -|x|.  Where the
+  // product nrm2 s0 leaves the normal range (tiny or huge columns, e.g. the
+  // rounding residue of an exactly cancelling column), r is formed from the
+  // separate roots of nrm2 and s0.
   static __device__ __forceinline__ void reflector(cplx x0, double s0, double nrm2, double& c,
                                                    cplx& w0, cplx& alpha) {
     const bool z0 = __double_as_longlong(s0) == 0;
     const bool zz = __double_as_longlong(nrm2) == 0;
-    const double rn = rsqrt(nrm2);
-    const double nrm = nrm2 * rn;
-    const double r0 = rsqrt(s0);
-    const double ax0 = s0 * r0;
-    const double phr = z0 ? 1.0 : x0.re * r0;
-    const double phi = z0 ? 0.0 : x0.im * r0;
-    const double a0 = z0 ? 0.0 : ax0;
-    const double cc = rsqrt(nrm * (nrm + a0));
-    const double t = cc * (a0 + nrm);
+    const double pr = z0 ? nrm2 : nrm2 * s0;
+    double r;
+    if (pr >= 1e-300 && pr <= 1e300)
+      r = nrm2 * rsqrt(pr);
+    else  // rare: |x| = nrm2 rsqrt(nrm2), 1/|x0| = rsqrt(s0), each in range
+      r = (nrm2 * rsqrt(nrm2)) * (z0 ? 1.0 : rsqrt(s0));
+    const double cc = rsqrt(z0 ? nrm2 : ::fma(s0, r, nrm2));
+    const double t = cc * (1.0 + r);
     c = zz ? 0.0 : cc;
-    w0 = zz ? cplx{0.0, 0.0} : cplx{phr * t, phi * t};
-    alpha = zz ? x0 : cplx{-nrm * phr, -nrm * phi};
+    w0 = zz ? cplx{0.0, 0.0} : (z0 ? cplx{cc * r, 0.0} : cplx{x0.re * t, x0.im * t});
+    alpha = zz ? x0 : (z0 ? cplx{-r, 0.0} : cplx{-r * x0.re, -r * x0.im});
   }
 };
 
 template <>
 struct Ops<double> {
   using R = double;
+  static constexpr int kMadSlots = 1;
   static __device__ __forceinline__ double zero() { return 0.0; }
   static __device__ __forceinline__ double one() { return 1.0; }
   static __device__ __forceinline__ double fma(double a, double b, double acc) { return ::fma(a, b, acc); }
@@ -182,6 +214,9 @@ struct Ops<double> {
   static __device__ __forceinline__ double absval(double a) { return fabs(a); }
   static __device__ __forceinline__ double load(const double* p, size_t i) { return __ldcg(p + i); }
   static __device__ __forceinline__ double from_re(double x) { return x; }
+  static __device__ __forceinline__ double conj_sel(double a, bool) { return a; }
+  static __device__ __forceinline__ double block_sum(double a, int c) { return bsum1(a, c); }
+  static __device__ __forceinline__ void block_sum2(double& a, double& b, int c) { bsum2(a, b, c); }
 
   static __device__ __forceinline__ void reflector(double x0, double s0, double nrm2, double& c,
                                                    double& w0, double& alpha) {
@@ -208,6 +243,7 @@ struct Ops<double> {
 template <>
 struct Ops<cplxf> {
   using R = float;
+  static constexpr int kMadSlots = 4;
   static __device__ __forceinline__ cplxf zero() { return cplxf{0.f, 0.f}; }
   static __device__ __forceinline__ cplxf one() { return cplxf{1.f, 0.f}; }
   static __device__ __forceinline__ cplxf fma(cplxf a, cplxf b, cplxf acc) {
@@ -260,6 +296,12 @@ struct Ops<cplxf> {
     return cplxf{(float)v.x, (float)v.y};
   }
   static __device__ __forceinline__ cplx widen(cplxf a) { return cplx{(double)a.re, (double)a.im}; }
+  static __device__ __forceinline__ cplxf conj_sel(cplxf a, bool c) { return cplxf{a.re, neg_if(a.im, c)}; }
+  static __device__ __forceinline__ cplxf block_sum(cplxf a, int c) {
+    bsum2(a.re, a.im, c);
+    return a;
+  }
+  static __device__ __forceinline__ void block_sum2(cplxf& a, cplxf& b, int c) { bsum4(a.re, a.im, b.re, b.im, c); }
   // the reflector of Ops<cplx>, in single precision
   static __device__ __forceinline__ void reflector(cplxf x0, float s0, float nrm2, float& c, cplxf& w0,
                                                    cplxf& alpha) {
@@ -283,6 +325,7 @@ struct Ops<cplxf> {
 template <>
 struct Ops<float> {
   using R = float;
+  static constexpr int kMadSlots = 1;
   static __device__ __forceinline__ float zero() { return 0.f; }
   static __device__ __forceinline__ float one() { return 1.f; }
   static __device__ __forceinline__ float fma(float a, float b, float acc) { return fmaf(a, b, acc); }
@@ -297,6 +340,9 @@ struct Ops<float> {
   static __device__ __forceinline__ float add(float a, float b) { return a + b; }
   static __device__ __forceinline__ float load(const double* p, size_t i) { return (float)__ldcg(p + i); }
   static __device__ __forceinline__ double widen(float a) { return (double)a; }
+  static __device__ __forceinline__ float conj_sel(float a, bool) { return a; }
+  static __device__ __forceinline__ float block_sum(float a, int c) { return bsum1(a, c); }
+  static __device__ __forceinline__ void block_sum2(float& a, float& b, int c) { bsum2(a, b, c); }
   static __device__ __forceinline__ void reflector(float x0, float s0, float nrm2, float& c, float& w0,
                                                    float& alpha) {
     const bool zz = __float_as_int(nrm2) == 0;
@@ -312,17 +358,71 @@ struct Ops<float> {
   }
 };
 
-// Sum over the G lanes of a group (butterfly: every lane of the group ends
-// with the bitwise-identical sum, since each stage adds a commuting pair).
+// Block sums over c lanes (c a power of two dividing the group width; the
+// block is lanes with equal lane / c).  Every lane of the block ends with
+// the bitwise-identical sums: each stage adds a commuting pair.  Two values
+// are reduced by splitting them over the two halves of the block first
+// (each half keeps one value and adds its partner's copy of it), so the
+// pair costs log2(c) additions per lane instead of 2 log2(c); four values
+// split twice.
+template <class R>
+__device__ __forceinline__ R bsum1(R x, int c) {
+  for (int o = c >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+template <class R>
+__device__ __forceinline__ void bsum2(R& x, R& y, int c) {
+  if (c == 1) return;
+  const int h = c >> 1;
+  const bool hi = (threadIdx.x & h) != 0;
+  R keep = hi ? y : x;
+  const R send = hi ? x : y;
+  keep += __shfl_xor_sync(kFull, send, h);
+  for (int o = h >> 1; o > 0; o >>= 1) keep += __shfl_xor_sync(kFull, keep, o);
+  const R other = __shfl_xor_sync(kFull, keep, h);
+  x = hi ? other : keep;
+  y = hi ? keep : other;
+}
+template <class R>
+__device__ __forceinline__ void bsum4(R& a, R& b, R& c2, R& d, int c) {
+  if (c <= 2) {
+    bsum2(a, b, c);
+    bsum2(c2, d, c);
+    return;
+  }
+  const int h = c >> 1, h2 = c >> 2;
+  const bool hi = (threadIdx.x & h) != 0, hi2 = (threadIdx.x & h2) != 0;
+  // stage 1: the lower half keeps (a, b), the upper half (c2, d)
+  R k0 = hi ? c2 : a, k1 = hi ? d : b;
+  const R s0 = hi ? a : c2, s1 = hi ? b : d;
+  k0 += __shfl_xor_sync(kFull, s0, h);
+  k1 += __shfl_xor_sync(kFull, s1, h);
+  // stage 2: each quarter keeps one value
+  R z = hi2 ? k1 : k0;
+  const R w = hi2 ? k0 : k1;
+  z += __shfl_xor_sync(kFull, w, h2);
+  for (int o = h2 >> 1; o > 0; o >>= 1) z += __shfl_xor_sync(kFull, z, o);
+  // quarter (hi, hi2) holds: (0,0) a, (0,1) b, (1,0) c2, (1,1) d
+  const R zh = __shfl_xor_sync(kFull, z, h), zq = __shfl_xor_sync(kFull, z, h2),
+          zb = __shfl_xor_sync(kFull, z, h | h2);
+  const R v00 = hi ? (hi2 ? zb : zh) : (hi2 ? zq : z);
+  const R v01 = hi ? (hi2 ? zh : zb) : (hi2 ? z : zq);
+  const R v10 = hi ? (hi2 ? zq : z) : (hi2 ? zb : zh);
+  const R v11 = hi ? (hi2 ? z : zq) : (hi2 ? zh : zb);
+  a = v00;
+  b = v01;
+  c2 = v10;
+  d = v11;
+}
+
+// Sum over the G lanes of a group.
 template <class R>
 __device__ __forceinline__ R group_sum(R x, int G) {
-  for (int o = G >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-  return x;
+  return bsum1(x, G);
 }
 template <class T>
 __device__ __forceinline__ T group_sum_t(T x, int G) {
-  for (int o = G >> 1; o > 0; o >>= 1) x = Ops<T>::add(x, Ops<T>::shfl_xor(x, o));
-  return x;
+  return Ops<T>::block_sum(x, G);
 }
 
 // First index >= lo that lane g of a G-lane group owns (index = g mod G).
@@ -359,256 +459,138 @@ __device__ __forceinline__ uint64_t next_comb(uint64_t x) {
 }
 
 // ---------------------------------------------------------------------------
-// Row- and column-blocked pieces of a Householder step.  A G-lane group
-// spreads a row range [lo, hi) over its lanes (lane g takes rows
-// lo + g, lo + g + G, ...) and walks the columns once for up to four of its
-// rows at a time, so each shared-memory load of a broadcast vector entry
-// feeds several independent complex FMAs.  Rows past `hi` are clamped to a
-// valid row for the loads and never stored.
+// The two passes of a Householder step over the active block.  GB300 retires
+// one warp-wide FP64 instruction per 64 cycles per SM sub-partition and
+// charges idle lanes in full, so both passes spread their multiply-adds
+// evenly over the G lanes of a group, whatever the shape of the block.
+//
+// Dot pass.  The N + L dot products of length L (L = N - k1)
+//   p_i  = sum_{j in K} A_ij w_j        (rows i = 0..N-1)
+//   t'_j = sum_{i in K} conj(w_i) A_ij  (columns j in K)
+// are cut into c pieces each; piece q of product tau is taken by lane
+// (tau c + q) mod G in round (tau c + q) / G, so the c pieces of a product
+// sit in c adjacent lanes of one round and are added by c-lane block sums.
+// c is chosen per step to minimise the rounds times (multiply-adds per piece
+// + combine stages).
 // ---------------------------------------------------------------------------
-#ifndef HAF_KBLK
-#define HAF_KBLK 4
-#endif
-#ifndef HAF_JUNROLL
-#define HAF_JUNROLL 1
-#endif
-#define HAF_STR_(x) #x
-#define HAF_STR(x) HAF_STR_(x)
-#define HAF_UNROLL_J _Pragma(HAF_STR(unroll HAF_JUNROLL))
-constexpr int kBlk = HAF_KBLK;
-
-// P[i] = sum_{j=k1}^{N-1} A_ij W[j] for NR rows starting at i0 (stride G).
-template <class T, int NR>
-__device__ __forceinline__ void rows_matvec(const T* __restrict__ tile, int ld, int k1, int N, int i0,
-                                            int hi, int G, const T* __restrict__ W, T* __restrict__ P) {
-  using O = Ops<T>;
-  const T* rp[NR];
-  T acc[NR];
-#pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    const int i = i0 + r * G;
-    rp[r] = tile + (i < hi ? i : hi - 1) * ld;
-    acc[r] = O::zero();
-  }
-  HAF_UNROLL_J
-  for (int j = k1; j < N; ++j) {
-    const T w = W[j];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = O::fma(rp[r][j], w, acc[r]);
-  }
-#pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    const int i = i0 + r * G;
-    if (i < hi) P[i] = acc[r];
-  }
-}
-
-// A_ij -= P[i] conj(W[j])  (+ W[i] TV[j] when TWO) for j in [k1, N), NR rows from i0.
-template <class T, int NR, bool TWO>
-__device__ __forceinline__ void rows_update(T* __restrict__ tile, int ld, int k1, int N, int i0, int hi,
-                                            int G, const T* __restrict__ W, const T* __restrict__ TV,
-                                            const T* __restrict__ P) {
-  using O = Ops<T>;
-  T* rp[NR];
-  T pr[NR], wr[NR];
-  bool ok[NR];
-#pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    const int i = i0 + r * G;
-    ok[r] = i < hi;
-    const int ic = ok[r] ? i : hi - 1;
-    rp[r] = tile + ic * ld;
-    pr[r] = P[ic];
-    wr[r] = TWO ? W[ic] : O::zero();
-  }
-  HAF_UNROLL_J
-  for (int j = k1; j < N; ++j) {
-    const T w = W[j];
-    const T t = TWO ? TV[j] : O::zero();
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      T a = rp[r][j];
-      a = O::fnma_cb(pr[r], w, a);
-      if (TWO) a = O::fnma(wr[r], t, a);
-      if (ok[r]) rp[r][j] = a;
-    }
-  }
-}
-
-// TV[j] = sum_{i=k1}^{N-1} conj(W[i]) A_ij - gam conj(W[j]) for NC columns from j0 (stride G).
-template <class T, int NC>
-__device__ __forceinline__ void cols_sum(const T* __restrict__ tile, int ld, int k1, int jhi, int j0, int G,
-                                         const T* __restrict__ W, T gam, T* __restrict__ TV, int N) {
-  using O = Ops<T>;
-  int jc[NC];
-  T acc[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    const int j = j0 + c * G;
-    jc[c] = j < jhi ? j : jhi - 1;
-    acc[c] = O::zero();
-  }
-  HAF_UNROLL_J
-  for (int i = k1; i < N; ++i) {
-    const T w = W[i];
-    const T* row = tile + i * ld;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = O::cfma(w, row[jc[c]], acc[c]);
-  }
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    const int j = j0 + c * G;
-    if (j < jhi) TV[j] = O::fnma_cb(gam, W[j], acc[c]);
-  }
-}
-
-// Rows [lo, hi): the first floor((hi-lo)/G) row slots give every lane a row
-// (register-blocked, four rows per column walk); the remaining rows (fewer
-// than G) are split by columns so that every lane gets an equal share.
 template <class T>
-__device__ __forceinline__ void range_matvec(const T* tile, int ld, int k1, int N, int lo, int hi, int g, int G,
-                                             const T* W, T* P, T* X) {
-  using O = Ops<T>;
-  const int full = (hi - lo) / G;
-  const int hb = lo + full * G;
-  for (int r0 = 0; r0 < full; r0 += kBlk) {
-    const int i0 = lo + g + r0 * G;
-    switch (min(kBlk, full - r0)) {
-#if HAF_KBLK > 4
-      case 8: rows_matvec<T, 8>(tile, ld, k1, N, i0, hb, G, W, P); break;
-      case 7: rows_matvec<T, 7>(tile, ld, k1, N, i0, hb, G, W, P); break;
-      case 6: rows_matvec<T, 6>(tile, ld, k1, N, i0, hb, G, W, P); break;
-      case 5: rows_matvec<T, 5>(tile, ld, k1, N, i0, hb, G, W, P); break;
-#endif
-      case 4: rows_matvec<T, 4>(tile, ld, k1, N, i0, hb, G, W, P); break;
-      case 3: rows_matvec<T, 3>(tile, ld, k1, N, i0, hb, G, W, P); break;
-      case 2: rows_matvec<T, 2>(tile, ld, k1, N, i0, hb, G, W, P); break;
-      default: rows_matvec<T, 1>(tile, ld, k1, N, i0, hb, G, W, P); break;
+__device__ __forceinline__ int dot_pieces(int ntask, int L, int G) {
+  constexpr int kMad = Ops<T>::kMadSlots;
+  int best = 0x7fffffff, best_lc = 0;
+  for (int lc = 0; (1 << lc) <= G; ++lc) {
+    const int c = 1 << lc;
+    const int rounds = (ntask * c + G - 1) / G;
+    const int len = (L + c - 1) >> lc;
+    const int cost = rounds * (kMad * len + lc);
+    if (cost < best) {
+      best = cost;
+      best_lc = lc;
     }
   }
-  const int rem = hi - hb;
-  if (rem > 0) {
-    // lane g: remainder row q = g % rem, column chunk c = g / rem of nc chunks
-    const int nc = G / rem;
-    const int q = g % rem, c = g / rem;
+  return best_lc;
+}
+
+template <class T>
+__device__ __forceinline__ void dot_pass(const T* __restrict__ tile, int ld, int N, int k1,
+                                         const T* __restrict__ W, T* __restrict__ P, T* __restrict__ TV,
+                                         int g, int G) {
+  using O = Ops<T>;
+  const int L = N - k1, ntask = N + L;
+  const int lc = dot_pieces<T>(ntask, L, G);
+  const int c = 1 << lc;
+  const int len = (L + c - 1) >> lc;
+  const int npiece = ntask << lc;
+  for (int p0 = 0; p0 < npiece; p0 += G) {
+    const int piece = p0 + g;
+    const bool live = piece < npiece;
+    const int tau = live ? (piece >> lc) : 0;
+    const int q = piece & (c - 1);
+    const bool col = tau >= N;
+    const int l0 = q * len;
+    const int l1 = live ? min(l0 + len, L) : l0;
+    const int a0 = col ? k1 * ld + (k1 + tau - N) : tau * ld + k1;  // >= 0 for every lane
+    const T* a = tile + a0;
+    const int stride = col ? ld : 1;
     T acc = O::zero();
-    if (c < nc) {
-      const T* row = tile + (hb + q) * ld;
-      for (int j = k1 + c; j < N; j += nc) acc = O::fma(row[j], W[j], acc);
-    }
-    X[g] = acc;
-    __syncwarp();
-    if (g < rem) {
-      T sum = X[g];
-      for (int cc = 1; cc < nc; ++cc) sum = O::add(sum, X[g + cc * rem]);
-      P[hb + g] = sum;
+    // not unrolled: unrolling puts adjacent W entries in one iteration, and a
+    // load vectoriser could then join them into one access wider than their
+    // 16-byte alignment
+#pragma unroll 1
+    for (int l = l0; l < l1; ++l) acc = O::fma(a[l * stride], O::conj_sel(W[k1 + l], col), acc);
+    acc = O::block_sum(acc, c);
+    if (live && q == 0) {
+      if (col)
+        TV[k1 + tau - N] = acc;
+      else
+        P[tau] = acc;
     }
   }
 }
 
-template <class T, bool TWO>
-__device__ __forceinline__ void range_update(T* tile, int ld, int k1, int N, int lo, int hi, int g, int G,
-                                             const T* W, const T* TV, const T* P) {
+// Update pass: A_ij -= q_i conj(w_j) for rows i < k1 and
+// A_ij -= q_i conj(w_j) + w_i t'_j for rows i in K, columns j in K; the
+// elements of each region are dealt to the lanes round robin.
+template <class T>
+__device__ __forceinline__ void update_pass(T* __restrict__ tile, int ld, int N, int k1, const T* __restrict__ W,
+                                            const T* __restrict__ TV, const T* __restrict__ Q, int g, int G) {
   using O = Ops<T>;
-  const int full = (hi - lo) / G;
-  const int hb = lo + full * G;
-  for (int r0 = 0; r0 < full; r0 += kBlk) {
-    const int i0 = lo + g + r0 * G;
-    switch (min(kBlk, full - r0)) {
-#if HAF_KBLK > 4
-      case 8: rows_update<T, 8, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
-      case 7: rows_update<T, 7, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
-      case 6: rows_update<T, 6, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
-      case 5: rows_update<T, 5, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
-#endif
-      case 4: rows_update<T, 4, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
-      case 3: rows_update<T, 3, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
-      case 2: rows_update<T, 2, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
-      default: rows_update<T, 1, TWO>(tile, ld, k1, N, i0, hb, G, W, TV, P); break;
-    }
-  }
-  // remainder rows [hb, hi): elements (i, j) spread round-robin over the lanes
   const int L = N - k1;
-  const int E = (hi - hb) * L;
-  int ii = hb, j = k1 + g;
-  while (j >= N && ii < hi) {
-    j -= L;
-    ++ii;
+  for (int e = g; e < k1 * L; e += G) {
+    const int i = (int)((unsigned)e / (unsigned)L), j = k1 + e - i * L;
+    T* a = tile + i * ld + j;
+    *a = O::fnma_cb(Q[i], W[j], *a);
   }
-  for (int e = g; e < E; e += G) {
-    T* a = tile + ii * ld + j;
-    T v = O::fnma_cb(P[ii], W[j], *a);
-    if (TWO) v = O::fnma(W[ii], TV[j], v);
-    *a = v;
-    j += G;
-    while (j >= N && ii < hi) {
-      j -= L;
-      ++ii;
-    }
+  for (int e = g; e < L * L; e += G) {
+    const int ii = (int)((unsigned)e / (unsigned)L);
+    const int i = k1 + ii, j = k1 + e - ii * L;
+    T* a = tile + i * ld + j;
+    const T v = O::fnma_cb(Q[i], W[j], *a);
+    *a = O::fnma(W[i], TV[j], v);
   }
 }
 
-// Columns [k1, N): full column slots blocked, the remaining columns (fewer
-// than G) split by rows with the partial sums combined through X.
+// gamma = w^H p_K and, with loops, aw = va . w (both over K), summed over the
+// group; then q_i = p_i - gamma w_i (i in K) and va <- va - aw conj(w).
 template <class T>
-__device__ __forceinline__ void range_colsum(const T* tile, int ld, int k1, int N, int g, int G, const T* W,
-                                             T gam, T* TV, T* X) {
+__device__ __forceinline__ void finish_step(int N, int k1, const T* __restrict__ W, T* __restrict__ P,
+                                            T* VA, bool loops, int g, int G) {
   using O = Ops<T>;
-  const int full = (N - k1) / G;
-  const int jb = k1 + full * G;
-  for (int c0 = 0; c0 < full; c0 += kBlk) {
-    const int j0 = k1 + g + c0 * G;
-    switch (min(kBlk, full - c0)) {
-#if HAF_KBLK > 4
-      case 8: cols_sum<T, 8>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
-      case 7: cols_sum<T, 7>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
-      case 6: cols_sum<T, 6>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
-      case 5: cols_sum<T, 5>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
-#endif
-      case 4: cols_sum<T, 4>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
-      case 3: cols_sum<T, 3>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
-      case 2: cols_sum<T, 2>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
-      default: cols_sum<T, 1>(tile, ld, k1, jb, j0, G, W, gam, TV, N); break;
-    }
+  T gam = O::zero(), aw = O::zero();
+  for (int i = k1 + g; i < N; i += G) {
+    gam = O::cfma(W[i], P[i], gam);
+    if (loops) aw = O::fma(VA[i], W[i], aw);
   }
-  const int rem = N - jb;
-  if (rem > 0) {
-    const int nc = G / rem;
-    const int q = g % rem, c = g / rem;
-    T acc = O::zero();
-    if (c < nc)
-      for (int i = k1 + c; i < N; i += nc) acc = O::cfma(W[i], tile[i * ld + jb + q], acc);
-    X[g] = acc;
-    __syncwarp();
-    if (g < rem) {
-      T sum = X[g];
-      for (int cc = 1; cc < nc; ++cc) sum = O::add(sum, X[g + cc * rem]);
-      TV[jb + g] = O::fnma_cb(gam, W[jb + g], sum);
-    }
+  if (loops)
+    O::block_sum2(gam, aw, G);
+  else
+    gam = O::block_sum(gam, G);
+  for (int i = k1 + g; i < N; i += G) {
+    P[i] = O::fnma(gam, W[i], P[i]);
+    if (loops) VA[i] = O::fnma_cb(aw, W[i], VA[i]);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Householder reduction to upper Hessenberg form, in place, by one G-lane
-// group.  Step k reflects rows/columns K = {k+1, ..., N-1}:
-//   w from column k; p = A[:,K] w; gamma = w^H p_K;
-//   t_j = sum_{i in K} conj(w_i) A_ij - gamma conj(w_j);
-//   A_ij -= p_i conj(w_j) (all rows) and -= w_i t_j (rows in K),
-// which is A <- (I - w w^H) A (I - w w^H) restricted to the active block.
-// With `loops` the reduction starts from b ("Krylov start"): a first
-// reflector on all N indices maps vb to alpha e_0 and is applied to A from
-// both sides and to va; the later steps act on indices >= 1, so vb stays
-// alpha e_0 while va <- va (I - w w^H) follows every step.  Then
-// H^{k-1} vb is supported on its first k entries (H is Hessenberg), which
-// is what makes the loop moments cheap.
+// group.  Step k reflects rows/columns K = {k+1, ..., N-1} with
+// H = I - w w^H, w from column k:
+//   p = A[:, K] w;  t'_j = sum_{i in K} conj(w_i) A_ij;  gamma = w^H p_K;
+//   q = p - gamma w (on K);  A_ij -= q_i conj(w_j) + w_i t'_j,
+// which is A <- H A H restricted to the active block (the w_i t'_j term only
+// on rows in K).  With `loops` the reduction starts from b ("Krylov start"):
+// a first reflector on all N indices maps vb to alpha e_0 and is applied to A
+// from both sides and to va; the later steps act on indices >= 1, so vb stays
+// alpha e_0 while va <- va (I - w w^H) follows every step.  Then H^{k-1} vb
+// is supported on its first k entries (H is Hessenberg), which is what makes
+// the loop moments cheap.
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__ W,
-                            T* __restrict__ P, T* __restrict__ TV, T* __restrict__ VA,
-                            T* __restrict__ VB, T* __restrict__ X, bool loops, int g, int G) {
+__device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__ W, T* __restrict__ P,
+                            T* __restrict__ TV, T* VA, T* VB, bool loops, int g,
+                            int G) {
   using O = Ops<T>;
+  using R = typename O::R;
   if (loops) {
-    using R = typename O::R;
     R sig = R(0);
     for (int i = 1 + g; i < N; i += G) sig = O::abs2_acc(VB[i], sig);
     sig = group_sum(sig, G);
@@ -620,28 +602,17 @@ __device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__
     for (int i = 1 + g; i < N; i += G) W[i] = O::scale(VB[i], c);
     if (g == 0) W[0] = w0;
     __syncwarp();
-    range_matvec<T>(tile, ld, 0, N, 0, N, g, G, W, P, X);  // p = A w
+    dot_pass<T>(tile, ld, N, 0, W, P, TV, g, G);
     __syncwarp();
-    T gam = O::zero();
-    for (int i = g; i < N; i += G) gam = O::cfma(W[i], P[i], gam);
-    gam = group_sum_t(gam, G);
+    finish_step<T>(N, 0, W, P, VA, true, g, G);
+    for (int i = g; i < N; i += G) VB[i] = (i == 0) ? alpha : O::zero();
     __syncwarp();
-    range_colsum<T>(tile, ld, 0, N, g, G, W, gam, TV, X);  // t_j, every column
-    T aw = O::zero();
-    for (int i = g; i < N; i += G) aw = O::fma(VA[i], W[i], aw);
-    aw = group_sum_t(aw, G);
-    for (int i = g; i < N; i += G) {
-      VA[i] = O::fnma_cb(aw, W[i], VA[i]);
-      VB[i] = (i == 0) ? alpha : O::zero();
-    }
-    __syncwarp();
-    range_update<T, true>(tile, ld, 0, N, 0, N, g, G, W, TV, P);  // every row, both sides
+    update_pass<T>(tile, ld, N, 0, W, TV, P, g, G);
     __syncwarp();
   }
   for (int k = 0; k + 2 < N; ++k) {
     const int k1 = k + 1;
     const int i2 = k + 2 + g;  // this lane's rows below the first reflected entry
-    using R = typename O::R;
     R sig = R(0);
     for (int i = i2; i < N; i += G) sig = O::abs2_acc(tile[i * ld + k], sig);
     sig = group_sum(sig, G);
@@ -656,22 +627,11 @@ __device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__
     // every lane has read x0 by now, so its entry may take alpha (column k
     // is outside the columns the rest of this step reads)
     if (g == 0) tile[k1 * ld + k] = alpha;
-    range_matvec<T>(tile, ld, k1, N, 0, N, g, G, W, P, X);  // p = A[:, K] w
+    dot_pass<T>(tile, ld, N, k1, W, P, TV, g, G);
     __syncwarp();
-    T gam = O::zero();
-    for (int i = k1 + g; i < N; i += G) gam = O::cfma(W[i], P[i], gam);
-    gam = group_sum_t(gam, G);
+    finish_step<T>(N, k1, W, P, VA, loops, g, G);
     __syncwarp();
-    range_colsum<T>(tile, ld, k1, N, g, G, W, gam, TV, X);  // t_j
-    if (loops) {  // va <- va (I - w w^H); vb = alpha e_0 is untouched (w_0 = 0)
-      T aw = O::zero();
-      for (int i = k1 + g; i < N; i += G) aw = O::fma(VA[i], W[i], aw);
-      aw = group_sum_t(aw, G);
-      for (int i = k1 + g; i < N; i += G) VA[i] = O::fnma_cb(aw, W[i], VA[i]);
-    }
-    __syncwarp();
-    range_update<T, false>(tile, ld, k1, N, 0, k1, g, G, W, TV, P);  // rows above K
-    range_update<T, true>(tile, ld, k1, N, k1, N, g, G, W, TV, P);   // rows in K
+    update_pass<T>(tile, ld, N, k1, W, TV, P, g, G);
     __syncwarp();
   }
 }
@@ -726,8 +686,8 @@ __device__ void loop_moments(const T* __restrict__ tile, int ld, int N, int h,
 // The products are folded into the upper triangle first (column by column,
 // from the diagonal upward), so c_{i,m} = H'_{i-1-m, i-1}.
 // The sum is evaluated "right-looking": once D_r is final, its terms
-//   D_{r+1}[j]   += D_r[j] - alpha_r D_r[j-1]
-//   D_i[t+i-r]   -= H'_{r, i-1} D_r[t]          (i = r+2..N)
+//   D_{r+1}[j]   += D_r[j]                       (j = 1..min(r,h))
+//   D_i[t+i-r]   -= H'_{r, i-1} D_r[t]          (i = r+1..N; H'_{r,r} = alpha_r)
 // are added to every later polynomial; the (i, t) pairs of one r are dealt
 // round robin over the group's lanes.  D_i[1..min(i,h)] for i < N accumulate in
 // row i of the tile, columns 0..i-1 (free after the reduction: entries
@@ -768,38 +728,31 @@ __device__ void labudde(T* __restrict__ tile, int ld, int N, int h, T* __restric
   }
   __syncwarp();
   for (int r = 0; r < N; ++r) {
-    const T alpha = tile[r * ld + r];
-    const T* Dr = tile + r * ld - 1;  // D_r[t] = Dr[t] for 1 <= t <= min(r,h)
-    const T* Hr = tile + r * ld;      // H'_{r, i-1} = Hr[i-1]
-    // (a) D_{r+1}[j] += D_r[j] - alpha_r D_r[j-1], j = 1..min(r+1,h); lanes over j
-    const int Ja = min(r + 1, h);
-    for (int j = 1 + g; j <= Ja; j += G) {
-      const T d = (j <= r) ? Dr[j] : O::zero();
-      const T dm = (j == 1) ? O::one() : Dr[j - 1];
-      T* a = dslot(tile, ld, N, DN, r + 1, j);
-      *a = O::fnma(alpha, dm, O::add(*a, d));
-    }
-    // (b) D_i[t+i-r] -= H'_{r,i-1} D_r[t] for rows i = r+2..imax and
-    //     t = 0..min(ra, h-(i-r)).  The (i, t) pairs, row by row, are dealt
-    //     to the lanes round robin (lane g takes pairs g, g+G, ...), so the
-    //     lanes' shares differ by at most one.
+    const T* Dr = tile + r * ld;  // D_r[t] = Dr[t - 1] for 1 <= t <= min(r,h); D_r[0] = 1
+    const T* Hr = tile + r * ld;  // H'_{r, i-1} = Hr[i-1]; H'_{r,r} = alpha_r
+    // D_i[t+i-r] -= H'_{r,i-1} D_r[t] for rows i = r+1..imax and
+    // t = 0..min(ra, h-(i-r)); row i = r+1 also takes D_r[t+1] (the
+    // D_{r+1}[j] += D_r[j] term).  The (i, t) units, row by row, are dealt to
+    // the lanes round robin (lane g takes units g, g+G, ...), so the lanes'
+    // shares differ by at most one and no two lanes write the same entry.
     const int ra = min(r, h);
     const int imax = min(N, h + r);
-    {
-      int i = r + 2, t = g;
+    int i = r + 1, t = g;
+    while (i <= imax && t > min(ra, h - (i - r))) {
+      t -= min(ra, h - (i - r)) + 1;
+      ++i;
+    }
+    while (i <= imax) {
+      const T dl = Dr[t > 0 ? t - 1 : 0];  // an address inside row r even when t = 0
+      const T d = (t == 0) ? O::one() : dl;
+      T* a = dslot(tile, ld, N, DN, i, i - r);  // D_i[t + i - r] = a[t]
+      T v = a[t];
+      if (i == r + 1 && t < ra) v = O::add(v, Dr[t]);
+      a[t] = O::fnma(Hr[i - 1], d, v);
+      t += G;
       while (i <= imax && t > min(ra, h - (i - r))) {
         t -= min(ra, h - (i - r)) + 1;
         ++i;
-      }
-      while (i <= imax) {
-        const T d = (t == 0) ? O::one() : Dr[t];
-        T* a = dslot(tile, ld, N, DN, i, i - r);  // D_i[t + i - r] = a[t]
-        a[t] = O::fnma(Hr[i - 1], d, a[t]);
-        t += G;
-        while (i <= imax && t > min(ra, h - (i - r))) {
-          t -= min(ra, h - (i - r)) + 1;
-          ++i;
-        }
       }
     }
     __syncwarp();
@@ -816,7 +769,7 @@ __device__ void labudde(T* __restrict__ tile, int ld, int N, int h, T* __restric
 // coefficient, one per lane.  Returns f = [lambda^h] g e.
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ T series(int N, int h, const T* __restrict__ DN, T* __restrict__ U, T* GS, T* AC,
+__device__ T series(int N, int h, const T* __restrict__ DN, T* U, T* GS, T* AC,
                     T* ES, T* AC2, bool loops, const double* __restrict__ tables, int g, int G) {
   using O = Ops<T>;
   const double* half = tables;         // half[k] = k/2
@@ -874,10 +827,10 @@ __device__ void loop_moments_tail(int N, int h, const T* __restrict__ DN, T* U, 
 // TB = TS; the FP32 mode runs TB in single precision and widens the
 // characteristic-polynomial coefficients (and loop moments) to FP64 before
 // the series, so only the O(N^3) part loses precision.
-// Per-subset shared-memory layout (subset_bytes in haf_internal.h):
-//   TB: tile N x ld, W, P, TV, VA, VB (N each), DN (h+1)
-//   mixed only: TB loop moments (h+1), then TS DN (h+1) at a 16-byte boundary
-//   TS: GS, AC, U, ES, AC2 (h+1 each); int pos[h]
+// Per-subset shared-memory layout: subset_layout in haf_internal.h (the
+// tile, whose first 4 (h+1) series elements take the power-series arrays
+// once La Budde is done; W, P, TV and, with loops, VA, VB; La Budde's output
+// and the loop moments; int pos[h]).
 // ---------------------------------------------------------------------------
 template <class TB, class TS>
 __device__ void process_chunk(const Job& job, const Chunk& ch, double* __restrict__ partial_out,
@@ -889,31 +842,26 @@ __device__ void process_chunk(const Job& job, const Chunk& ch, double* __restric
   const int n = job.n, h = n >> 1, m = ch.m, N = 2 * m, G = ch.G, S = 32 / G, ld = ch.ld;
   const int s = lane / G, g = lane - s * G;
   const bool loops = job.loops != 0;
-  const int sub_bytes = subset_bytes(N, ld, h, (int)sizeof(TB), (int)sizeof(TS), kMixed);
-  unsigned char* base = wbase + s * sub_bytes;
+  const SubsetLayout lay = subset_layout(N, ld, h, (int)sizeof(TB), (int)sizeof(TS), kMixed, loops);
+  unsigned char* base = wbase + s * lay.total;
   TB* tile = reinterpret_cast<TB*>(base);
-  TB* W = tile + N * ld;
+  TB* W = reinterpret_cast<TB*>(base + lay.vec);
   TB* P = W + N;
   TB* TV = P + N;
-  TB* VA = TV + N;
-  TB* VB = VA + N;
-  TB* DNb = VB + N;
-  TS* DN;
-  TB* Ub;
-  if constexpr (kMixed) {
-    Ub = DNb + (h + 1);
-    DN = reinterpret_cast<TS*>(base + subset_bulk_bytes(N, ld, h, (int)sizeof(TB)));
-  } else {
-    DN = DNb;
-    Ub = nullptr;
-  }
-  TS* GS = DN + (h + 1);
+  TB* DNb = reinterpret_cast<TB*>(base + lay.dnb);
+  TS* DN = reinterpret_cast<TS*>(base + lay.dn);
+  // the loop-hafnian arrays exist only with loops; otherwise they alias
+  // arrays of the subset (never written then), so that every pointer stays
+  // inside the subset's region
+  TB* VA = loops ? TV + N : W;
+  TB* VB = loops ? TV + 2 * N : W;
+  TB* Ub = loops ? reinterpret_cast<TB*>(base + lay.ub) : DNb;
+  TS* U = loops ? reinterpret_cast<TS*>(base + lay.u) : DN;
+  TS* GS = reinterpret_cast<TS*>(base);
   TS* AC = GS + (h + 1);
-  TS* U = AC + (h + 1);
-  TS* ES = U + (h + 1);
+  TS* ES = AC + (h + 1);
   TS* AC2 = ES + (h + 1);
-  if constexpr (!kMixed) Ub = U;
-  int* pos = reinterpret_cast<int*>(AC2 + (h + 1));
+  int* pos = reinterpret_cast<int*>(base + lay.pos);
   const bool neg = ((h - m) & 1) != 0;
   const bool term_mode = terms_out != nullptr;
 
@@ -954,7 +902,7 @@ __device__ void process_chunk(const Job& job, const Chunk& ch, double* __restric
       }
     }
     __syncwarp();
-    householder<TB>(tile, ld, N, W, P, TV, VA, VB, DNb, loops, g, G);  // DN area as scratch
+    householder<TB>(tile, ld, N, W, P, TV, VA, VB, loops, g, G);
     if (loops) loop_moments<TB>(tile, ld, N, h, VA, VB, W, TV, Ub, g, G);
     labudde<TB>(tile, ld, N, h, DNb, g, G);
     if constexpr (kMixed) {

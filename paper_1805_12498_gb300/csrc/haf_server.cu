@@ -585,6 +585,13 @@ int haf_server_poll(haf_server* s, uint64_t ticket, double* out, haf_info* info,
     info->subsets = j.subsets;
     info->seconds = j.done_t - j.submit_t;
     info->launches = s->launches;
+    {
+      const double v = std::hypot(out[0], out[1]);
+      const double a = j.result[4];
+      info->rel_err_bound = a == 0.0 ? 0.0 : (v == 0.0 ? HUGE_VAL : HAF_FP64_REL_TOL * a / v);
+    }
+    info->precision_mode = 0;
+    info->reserved = 0;
   }
   if (j.uploaded) cudaEventDestroy(j.uploaded);
   s->jobs.erase(it);

@@ -75,7 +75,11 @@ def test_precision_limits_match_the_header():
     src = open(os.path.join(ROOT, "include", "hafnian_gb300.h")).read()
     max_n = int(re.search(r"#define HAF_FP32_MAX_N (\d+)", src).group(1))
     tol = float(re.search(r"#define HAF_FP32_REL_TOL ([0-9.e+-]+)", src).group(1))
+    tol64 = float(re.search(r"#define HAF_FP64_REL_TOL ([0-9.e+-]+)", src).group(1))
+    gate = float(re.search(r"#define HAF_FP32_MAX_REL_ERR ([0-9.e+-]+)", src).group(1))
+    code = int(re.search(r"#define HAF_EACCURACY \((-\d+)\)", src).group(1))
     assert hg.HAF_FP32_MAX_N == max_n and hg.HAF_FP32_REL_TOL == tol
+    assert hg.HAF_FP64_REL_TOL == tol64 and hg.HAF_FP32_MAX_REL_ERR == gate and hg._native.HAF_EACCURACY == code
     assert int(re.search(r"#define HAF_FLAG_FP32 \(1u << (\d+)\)", src).group(1)) == 2
     with pytest.raises(ValueError):
         hg._flags(precision="fp16")

@@ -31,16 +31,22 @@ def test_every_subset_planned_once(n, flags, wpb):
     assert w == sorted(w, reverse=True) and w[0] <= wpb and all(x in (4, 8, 16) for x in w)
 
 
-def _fits(N, h, sb, ss, mixed, warp_bytes):
-    """Smallest-G fit of one subset (mirror of the planner's rule, written
-    from the layout the kernel documents)."""
+def _r16(b):
+    return (b + 15) // 16 * 16
+
+
+def _fits(N, h, sb, ss, mixed, warp_bytes, loops=False):
+    """One subset fits a warp slice (mirror of the planner's rule, written
+    from the layout the kernel documents: the N x ld tile, which also holds
+    the four power-series arrays once La Budde is done; W, P, TV and, for
+    lhaf, VA, VB; La Budde's output (and the loop moments); in the FP32 mode
+    their FP64 copies; the pair list)."""
     for ld in (N + 1, N):
+        b = _r16(max(N * ld * sb, 4 * (h + 1) * ss))
+        b += (5 if loops else 3) * N * sb + (2 if loops else 1) * (h + 1) * sb
         if mixed:
-            bulk = ((N * ld + 5 * N + 2 * (h + 1)) * sb + 15) // 16 * 16
-            b = bulk + 6 * (h + 1) * ss + 4 * h
-        else:
-            b = (N * ld + 5 * N + 6 * (h + 1)) * sb + 4 * h
-        b = (b + 15) // 16 * 16
+            b = _r16(b) + (2 if loops else 1) * (h + 1) * ss
+        b = _r16(_r16(b) + 4 * h)
         if b <= warp_bytes:
             return True
     return False
@@ -48,13 +54,18 @@ def _fits(N, h, sb, ss, mixed, warp_bytes):
 
 def test_large_tiles_fall_back_to_fewer_warps():
     # complex128 at n = 48: with 8 warps per CTA (29,056 B per warp) the tiles
-    # of |Z| >= 20 (N >= 40) do not fit, so they form a 4-warp launch
+    # of |Z| >= 21 (N >= 42) do not fit, so they form a 4-warp launch
     h = 24
     s = stats(48, 0, 8)
     assert int(s[1]) == 2 and list(s[2:4]) == [8, 4]
     big = sum(comb(h, m) for m in range(1, h + 1) if not _fits(2 * m, h, 16, 16, False, 29056))
-    assert big == sum(comb(h, m) for m in range(20, h + 1))
+    assert big == sum(comb(h, m) for m in range(21, h + 1))
     assert s[6] == big and s[5] == 2 ** h - 1 - big
+    # the loop hafnian's extra vectors push |Z| = 20 out as well
+    s = stats(48, _native.HAF_FLAG_LOOPS, 8)
+    big = sum(comb(h, m) for m in range(1, h + 1) if not _fits(2 * m, h, 16, 16, False, 29056, True))
+    assert big == sum(comb(h, m) for m in range(20, h + 1))
+    assert s[6] == big
     # with 4 warps per CTA everything fits one launch
     s = stats(48, 0, 4)
     assert int(s[1]) == 1 and s[2] == 4

@@ -2,7 +2,11 @@
 Householder reduction, loop moments and La Budde recurrence, FP64 series
 and double-double subset sum.  Its error is stated relative to
 abs_sum = sum_Z |f(Z)| (HAF_FP32_REL_TOL) and checked against the oracle
-(small n) and against the FP64 path (which the oracle pins) at larger n."""
+(small n) and against the FP64 path (which the oracle pins) at larger n.
+Because the subset sum cancels, a whole-matrix FP32-bulk call is refused
+(HAF_EACCURACY) when HAF_FP32_REL_TOL * abs_sum / |value| exceeds
+HAF_FP32_MAX_REL_ERR; the tests of the error itself read the value that a
+refused call still writes."""
 import json
 import os
 
@@ -20,6 +24,15 @@ pytestmark = pytest.mark.gpu
 TOL32 = hg.HAF_FP32_REL_TOL
 
 
+def _fp32(A, loops=False, real=None):
+    """The FP32-bulk result and report, whether the accuracy gate admits it
+    or refuses it (a refused call still writes them)."""
+    try:
+        return hg.haf_info(A, loops, real=real, precision="fp32")
+    except hg.HafAccuracyError as e:
+        return e.result
+
+
 def _gbs(n, seed):
     B = inputs.gbs_kernel(32, 0.88, seed)
     return inputs.repeat_submatrix(B, inputs.click_pattern(n, 32, inputs.rng(seed + 7)))
@@ -30,7 +43,7 @@ def _gbs(n, seed):
 def test_fp32_against_oracle_small(n, loops):
     for A in (inputs.complex_gaussian_symmetric(n, 70 + n), _gbs(n, 80 + n)):
         want, scale = oracle.haf_formula(A, loops)
-        got = hg.haf_info(A, loops, precision="fp32")
+        got = _fp32(A, loops)
         assert abs(got.value - want) <= TOL32 * scale, (n, loops, got.value, want, scale)
         assert got.abs_sum == pytest.approx(scale, rel=1e-4)
 
@@ -39,7 +52,7 @@ def test_fp32_against_oracle_small(n, loops):
 def test_fp32_real_against_oracle(loops):
     A = inputs.real_gaussian_symmetric(14, 91)
     want, scale = oracle.haf_formula(A, loops)
-    got = hg.haf_info(A, loops, real=True, precision="fp32")
+    got = _fp32(A, loops, real=True)
     assert abs(got.value - want) <= TOL32 * scale
 
 
@@ -48,7 +61,7 @@ def test_fp32_against_fp64(n):
     for A in (inputs.complex_gaussian_symmetric(n, 1000 + n), _gbs(n, 2000 + n)):
         for loops in (False, True):
             a = hg.haf_info(A, loops)
-            b = hg.haf_info(A, loops, precision="fp32")
+            b = _fp32(A, loops)
             assert abs(a.value - b.value) <= TOL32 * a.abs_sum, (n, loops)
             assert b.abs_sum == pytest.approx(a.abs_sum, rel=1e-4)
 
@@ -62,7 +75,7 @@ def test_fp32_against_stored_oracle_sums():
         cases = json.load(f)["cases"]
     for c in cases:
         A = golden_cases.case_matrix(c)
-        got = hg.haf_info(A, loops=c["loops"], real=c["real"], precision="fp32")
+        got = _fp32(A, c["loops"], real=c["real"])
         want = complex(c["re"], c["im"])
         assert abs(got.value - want) <= TOL32 * c["abs_sum"], (c["name"], got.value, want, c["abs_sum"])
         assert got.abs_sum == pytest.approx(c["abs_sum"], rel=1e-4), c["name"]
@@ -84,9 +97,12 @@ def test_fp32_terms_at_n48_against_oracle():
 def test_fp32_batched_and_launch_forms():
     torch = pytest.importorskip("torch")
     _, mats = inputs.gbs_batch(24, seed=3, n_min=4, n_max=20)
-    vals = hg.haf_batched(mats, precision="fp32")
+    try:
+        vals = hg.haf_batched(mats, precision="fp32")
+    except hg.HafAccuracyError as e:  # some n = 14-20 matrices cancel too much
+        vals = e.result[0]
     for M, v in zip(mats, vals):
-        s = hg.haf_info(M, precision="fp32")
+        s = _fp32(M)
         assert abs(v - s.value) <= 1e-12 * s.abs_sum
     n = 20
     A = inputs.complex_gaussian_symmetric(n, 5)
@@ -100,7 +116,7 @@ def test_fp32_batched_and_launch_forms():
     hg.haf_launch(dA.data_ptr(), n, out.data_ptr(), wptr, ws, st.cuda_stream, precision="fp32")
     st.synchronize()
     o = out.cpu().numpy()
-    r = hg.haf_info(A, precision="fp32")
+    r = _fp32(A)
     assert complex(o[0] + o[2], o[1] + o[3]) == r.value
 
 
@@ -113,3 +129,37 @@ def test_fp32_mode_flags_and_limits():
         B = inputs.complex_gaussian_symmetric(hg.HAF_FP32_MAX_N + 2, 1)
         with pytest.raises(hg.HafError):
             hg.haf_info(B, precision="fp32")
+
+
+def test_fp32_accuracy_gate_admits_and_refuses():
+    """The value-relative gate: a call is admitted exactly when the estimate
+    HAF_FP32_REL_TOL * abs_sum / |value| is within HAF_FP32_MAX_REL_ERR, and
+    then its error against the oracle is within that bound; the complex
+    Gaussian n = 40 hafnian (stored oracle sum), whose FP32-bulk value has
+    no correct digit, is refused."""
+    admitted = 0
+    for n in (4, 6, 8, 10, 12):
+        for A in (np.ones((n, n), dtype=complex), inputs.complex_gaussian_symmetric(n, 300 + n),
+                  _gbs(n, 310 + n)):
+            want, scale = oracle.haf_formula(A)
+            est = TOL32 * scale / abs(want)
+            if est <= hg.HAF_FP32_MAX_REL_ERR:
+                r = hg.haf_info(A, precision="fp32")
+                assert r.precision_mode == 1 and r.rel_err_bound <= hg.HAF_FP32_MAX_REL_ERR
+                assert abs(r.value - want) <= r.rel_err_bound * abs(want), (n, r.value, want)
+                admitted += 1
+            elif est > 2 * hg.HAF_FP32_MAX_REL_ERR:  # clear of the boundary
+                with pytest.raises(hg.HafAccuracyError):
+                    hg.haf_info(A, precision="fp32")
+    assert admitted >= 10
+    A = golden_cases.case_matrix({"n": 40, "seed": 40, "real": False})
+    want, scale = golden_cases.stored("cgauss40_haf")
+    with pytest.raises(hg.HafAccuracyError) as e:
+        hg.haf_info(A, precision="fp32")
+    r = e.value.result
+    assert e.value.code == hg._native.HAF_EACCURACY and r.precision_mode == 1
+    assert r.rel_err_bound > 1 and abs(r.value - want) > hg.HAF_FP32_MAX_REL_ERR * abs(want)
+    assert abs(r.value - want) <= TOL32 * scale  # still within the stated error per unit of abs_sum
+    # FP64 reports its own estimate and is never gated
+    r64 = hg.haf_info(A)
+    assert r64.precision_mode == 0 and abs(r64.value - want) <= r64.rel_err_bound * abs(want)
