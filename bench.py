@@ -215,6 +215,7 @@ def precision_leg(seed: int, value48=None):
             t32 = time.perf_counter() - t
             d = abs(r32.value - v64)
             masks = inputs.random_masks(n // 2, 1024, seed=seed + n)
+            masks = masks[masks != 0]  # the empty subset's term is 0
             f64 = hg.haf_terms(A, masks)
             rel = np.abs(hg.haf_terms(A, masks, precision="fp32") - f64) / np.abs(f64)
             rows.append({"input": kind, "n": n, "err_over_abs_sum": d / a64,
@@ -434,11 +435,12 @@ def run_shard(args, hg, inputs, torch, dist, world: int, rank: int, dev):
 
     for _ in range(max(1, args.warmup)):
         hg.haf_part(A, rank, world)
-    times, value, abs_sum = [], None, None
+    times, value, abs_sum, launches = [], None, None, 0
     for _ in range(args.steps):
         barrier()
         t0 = time.perf_counter()
-        rec = hg.haf_part(A, rank, world)
+        rec, info = hg.haf_part(A, rank, world, with_info=True)
+        launches += int(info.launches)
         t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
         recs = torch.tensor(rec, dtype=torch.float64, device=dev)
         if world > 1:
@@ -470,7 +472,7 @@ def run_shard(args, hg, inputs, torch, dist, world: int, rank: int, dev):
                                      "peak = DFMA probe of rank 0 (of measured)"},
                 "e2e": {"value": 2 ** h / s_step, "unit": UNIT, "h2d_bytes_per_step": world * n * n * 16,
                         "d2h_bytes_per_step": world * 40},
-                "gpu_launches": None}
+                "gpu_launches": launches}
         print(json.dumps(line), flush=True)
 
 
@@ -505,9 +507,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gbs-batch", type=int, default=4096,
                     help="GBS-shaped batch size for the batched leg (0 skips it)")
-    ap.add_argument("--serve-requests", type=int, default=1200,
+    ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests in the serving leg (0 skips it)")
-    ap.add_argument("--serve-nmax", type=int, default=40)
+    ap.add_argument("--serve-nmax", type=int, default=52,
+                    help="largest n of the serving mix (n even in [8, nmax], P(n) ~ 2^(-n/8))")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32-vs-FP64 precision leg")
     ap.add_argument("--no-lhaf", action="store_true", help="skip the loop-hafnian leg")
     ap.add_argument("--shard", action="store_true",

@@ -85,18 +85,21 @@ extern "C" {
  * single precision (complex64 / float32) while the power series, f(Z) and
  * the double-double subset sum stay FP64 (Sec. 4 finds that the precision of
  * the eigenvalue step dominates the error; this mode trades it for speed).
- * Its error is bounded in practice by HAF_FP32_REL_TOL * abs_sum.  A
+ * Its error measured against FP64 over complex and real Gaussian, GBS and
+ * all-ones inputs at n = 2..40 (haf and lhaf) stayed below 1.2e-5 * abs_sum;
+ * HAF_FP32_REL_TOL = 3e-5 is that bound with a margin.  It is an empirical
+ * bound: a summand whose loop terms cancel internally can exceed it.  A
  * whole-matrix call in this mode is gated on the value: when rel_err_bound
  * exceeds HAF_FP32_MAX_REL_ERR it returns HAF_EACCURACY (the value and the
  * report are still written; recompute without HAF_FLAG_FP32 for a result in
- * FP64).  Inputs with heavy cancellation -- random Gaussian or GBS matrices
- * beyond n of about 16 -- are refused; inputs with little cancellation are
- * admitted at any n <= HAF_FP32_MAX_N.  The device-pointer form haf_launch
+ * FP64).  The gate admits inputs with abs_sum / |value| <= 33: in practice
+ * random Gaussian or GBS matrices up to n of about 8-10; larger inputs with
+ * heavy cancellation are refused.  The device-pointer form haf_launch
  * and the part records of haf_part are not gated (their value is on the
  * device, or is only a part of the sum). */
 #define HAF_FP32_MAX_N 56
 #define HAF_FP64_REL_TOL 1e-13
-#define HAF_FP32_REL_TOL 2e-6
+#define HAF_FP32_REL_TOL 3e-5
 #define HAF_FP32_MAX_REL_ERR 1e-3
 
 /* Per-call report. */

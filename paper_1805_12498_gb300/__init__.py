@@ -34,7 +34,7 @@ __all__ = ["haf", "lhaf", "haf_info", "haf_batched", "haf_terms", "workspace_byt
 # estimated relative error above which an FP32-bulk result is refused.
 HAF_FP32_MAX_N = 56
 HAF_FP64_REL_TOL = 1e-13
-HAF_FP32_REL_TOL = 2e-6
+HAF_FP32_REL_TOL = 3e-5
 HAF_FP32_MAX_REL_ERR = 1e-3
 
 
@@ -179,10 +179,11 @@ def haf_launch_noalloc(dA_ptr: int, n: int, d_out_ptr: int, stream_ptr: int = 0,
 
 
 def haf_part(A, part: int, nparts: int, loops: bool = False, real: bool | None = None,
-             precision: str = "fp64") -> np.ndarray:
+             precision: str = "fp64", with_info: bool = False):
     """Record {re_hi, im_hi, re_lo, im_lo, abs_sum} of part `part` of `nparts`
     of the subset sum (each size class cut into nparts contiguous slices);
-    runs on the current CUDA device.  Combine the parts with ``combine``."""
+    runs on the current CUDA device.  Combine the parts with ``combine``.
+    With ``with_info`` also the call's report (subsets, seconds, launches)."""
     tuning.ensure_loaded()
     if real is None:
         real = not np.iscomplexobj(A)
@@ -192,6 +193,8 @@ def haf_part(A, part: int, nparts: int, loops: bool = False, real: bool | None =
     info = _native.HafInfo()
     _native.check(_native.lib().haf_part(A.ctypes.data_as(_native._DP), A.shape[0], flags, part, nparts,
                                          rec.ctypes.data_as(_native._DP), ctypes.byref(info)))
+    if with_info:
+        return rec, _info(complex(rec[0] + rec[2], rec[1] + rec[3]), info)
     return rec
 
 

@@ -643,7 +643,29 @@ __device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__
 // supported on entries 0..k-1: step k computes rows 0..k-1 of H y_{k-1}
 // from columns 0..k-2 only (row i from column max(i-1, 0)), about k^2/2
 // multiply-adds instead of N^2/2.  Y0, Y1: scratch vectors of length N.
+// Row i has k - max(i, 1) entries, so rows p and k-1-p together have about
+// k + 1: each such pair is one task, cut into c pieces taken by c adjacent
+// lanes (c chosen per k as in the dot pass); a piece crosses from the first
+// row to the second at most once, and the two partial sums are added over
+// the c lanes.
 // ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ int moment_pieces(int npair, int k, int G) {
+  constexpr int kMad = Ops<T>::kMadSlots;
+  int best = 0x7fffffff, best_lc = 0;
+  for (int lc = 0; (1 << lc) <= G; ++lc) {
+    const int c = 1 << lc;
+    const int rounds = (npair * c + G - 1) / G;
+    const int len = (k + 1 + c - 1) >> lc;
+    const int cost = rounds * (kMad * len + (lc >= 2 ? lc + 1 : 2 * lc) + 2 * kMad);
+    if (cost < best) {
+      best = cost;
+      best_lc = lc;
+    }
+  }
+  return best_lc;
+}
+
 template <class T>
 __device__ void loop_moments(const T* __restrict__ tile, int ld, int N, int h,
                              const T* __restrict__ VA, const T* __restrict__ VB, T* Y0, T* Y1,
@@ -656,16 +678,44 @@ __device__ void loop_moments(const T* __restrict__ tile, int ld, int N, int h,
   }
   for (int k = 2; k <= kmax; ++k) {
     __syncwarp();
+    const int npair = (k + 1) >> 1;
+    const int lc = moment_pieces<T>(npair, k, G);
+    const int c = 1 << lc;
+    const int len = (k + 1 + c - 1) >> lc;
     T uk = O::zero();
-    // rows 0..k-1 in zig-zag order over the lanes (row i has k - max(i, 1) entries)
-    for (int q = 0; q * G < k; ++q) {
-      const int i = q * G + ((q & 1) ? (G - 1 - g) : g);
-      if (i >= k) continue;
-      const T* row = tile + i * ld;
-      T acc = O::zero();
-      for (int j = (i > 0 ? i - 1 : 0); j <= k - 2; ++j) acc = O::fma(row[j], Y0[j], acc);
-      Y1[i] = acc;
-      uk = O::fma(VA[i], acc, uk);
+    for (int p0 = 0; p0 < (npair << lc); p0 += G) {
+      const int piece = p0 + g;
+      const bool live = piece < (npair << lc);
+      const int p = live ? (piece >> lc) : 0;
+      const int q = piece & (c - 1);
+      const int ra = p, rb = k - 1 - p;
+      const int la = (ra == 0) ? k - 1 : k - ra;            // entries of row ra
+      const int lb = (rb == ra) ? 0 : ((rb == 0) ? k - 1 : k - rb);
+      const int ja = ra > 0 ? ra - 1 : 0, jb = rb > 0 ? rb - 1 : 0;
+      const int lo = q * len;
+      const int hi = live ? min(lo + len, la + lb) : lo;
+      T acc = O::zero(), acc_a = O::zero();
+      for (int e = lo; e < hi; ++e) {
+        if (e == la) {  // the piece passes from row ra to row rb
+          acc_a = acc;
+          acc = O::zero();
+        }
+        const bool in_a = e < la;
+        const int i = in_a ? ra : rb;
+        const int j = in_a ? ja + e : jb + (e - la);
+        acc = O::fma(tile[i * ld + j], Y0[j], acc);
+      }
+      T sa = (lo >= la) ? O::zero() : ((hi <= la) ? acc : acc_a);
+      T sb = (hi <= la) ? O::zero() : acc;
+      O::block_sum2(sa, sb, c);
+      if (live && q == 0) {
+        Y1[ra] = sa;
+        uk = O::fma(VA[ra], sa, uk);
+        if (rb != ra) {
+          Y1[rb] = sb;
+          uk = O::fma(VA[rb], sb, uk);
+        }
+      }
     }
     uk = group_sum_t(uk, G);
     if (g == 0) U[k] = uk;

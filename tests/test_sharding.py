@@ -94,8 +94,9 @@ def _rank_main(rank, world, port, n, q):
     rec = torch.tensor([re, im, 0.0, 0.0, float(np.sum(np.abs(f)))], dtype=torch.float64)
     out = [torch.zeros(5, dtype=torch.float64) for _ in range(world)]
     dist.all_gather(out, rec)
-    v, s = hg.combine(torch.stack(out).numpy())
-    q.put((rank, v, s))
+    recs = torch.stack(out).numpy()
+    v, s = hg.combine(recs)
+    q.put((rank, v, s, recs))
     dist.destroy_process_group()
 
 
@@ -113,9 +114,14 @@ def test_two_gloo_ranks_combine_to_the_whole_sum():
         p.join(timeout=60)
         assert p.exitcode == 0
     want, scale = oracle.haf_formula(inputs.complex_gaussian_symmetric(n, 77))
-    for rank, v, s in res:
+    for rank, v, s, recs in res:
         assert abs(v - want) <= 1e-12 * scale
         assert s == pytest.approx(scale, rel=1e-12)
+    # every rank combines the same records in part order: bit-identical
+    # results, equal to a single process combining them in part order
+    assert res[0][1] == res[1][1] and res[0][2] == res[1][2]
+    v_local, s_local = hg.combine(res[0][3])
+    assert v_local == res[0][1] and s_local == res[0][2]
 
 
 @pytest.mark.gpu
@@ -128,3 +134,23 @@ def test_parts_on_one_gpu_combine_to_single_call(n, loops):
         v, s = hg.combine(recs)
         assert abs(v - whole.value) <= 1e-10 * whole.abs_sum
         assert s == pytest.approx(whole.abs_sum, rel=1e-9)
+
+
+@pytest.mark.gpu
+def test_bench_shard_path_matches_single_call(capsys):
+    """bench.py --shard at one rank: the sharded path (part records and the
+    combine) gives the single call's value."""
+    import argparse
+    import json
+    import sys
+
+    import torch
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    args = argparse.Namespace(n=24, seed=5, steps=1, warmup=1)
+    bench.run_shard(args, hg, inputs, torch, None, 1, 0, torch.device("cuda", 0))
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    whole = hg.haf_info(inputs.complex_gaussian_symmetric(24, 5))
+    got = complex(line["result"]["re"], line["result"]["im"])
+    assert abs(got - whole.value) <= 1e-10 * whole.abs_sum
+    assert line["scaling"] == "strong" and line["n_gpus"] == 1
