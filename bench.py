@@ -291,11 +291,11 @@ def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
         reqs.append((inputs.repeat_submatrix(B, inputs.click_pattern(n, 32, g)), bool(g.integers(0, 2))))
     with hg.Server() as srv:
         for M, loops in reqs[:16]:  # warm the resident kernel and the plans
-            srv.poll(srv.submit(M, loops), timeout_s=120)
+            srv.poll(srv.submit(M, loops), timeout_s=3600)
         t = time.perf_counter()
         tickets = [srv.submit(M, loops) for M, loops in reqs]
         for tk in tickets:
-            srv.poll(tk, timeout_s=120)
+            srv.poll(tk, timeout_s=3600)
         capacity = requests / (time.perf_counter() - t)
         rate = load * capacity
         gaps = g.exponential(1.0 / rate, size=requests)
@@ -325,7 +325,7 @@ def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
             if not ready:
                 time.sleep(0.0005)
                 continue
-            lat.append(srv.poll(tk, timeout_s=120).seconds)
+            lat.append(srv.poll(tk, timeout_s=3600).seconds)
             k += 1
         thr.join()
         wall = time.perf_counter() - t0

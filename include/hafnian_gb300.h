@@ -206,8 +206,12 @@ int haf_launch(const double* dA, int64_t n, uint32_t flags, double* d_out, void*
  *           work and returns before the result is ready.
  * n must be even with 2 <= n <= HAF_MAX_N; anything else returns HAF_EINVAL
  * with a message.  The first call on a device looks up the array's device
- * address and sets kernel attributes; make that first call before any stream
- * capture.  All calls share the one array: calls whose work overlaps on the
+ * address and sets kernel attributes; with CUDA's lazy module loading (the
+ * default) it is also the call that loads the library's device code and
+ * reserves the array, which takes device memory.  Make that first call at
+ * start-up, before any stream capture and before a memory pool claims the
+ * device's memory.  The call plans with the launch shape that haf_launch
+ * uses for the same n and flags (haf_tune / haf_tune_set, else the default).  All calls share the one array: calls whose work overlaps on the
  * GPU (e.g. on two unordered streams) race and corrupt each other's results,
  * so order them on one stream or synchronise between them.
  * ---------------------------------------------------------------------- */

@@ -755,19 +755,23 @@ __device__ void labudde(T* __restrict__ tile, int ld, int N, int h, T* __restric
   // Fold the subdiagonal products into the upper triangle, row by row:
   // H'_{a,b} = H_{a,b} s_{a+1} s_{a+2} ... s_b (s_l = H_{l,l-1}).  Row a has
   // N-1-a entries, so rows a and N-2-a together have N: each lane takes such
-  // pairs (the middle row alone), which keeps the lanes' work equal.
+  // a pair (the middle row alone) and walks it as one loop of N entries, so
+  // every lane of a round runs the same number of iterations.
   for (int p = g; p < (N >> 1); p += G) {
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int a = half ? N - 2 - p : p;
-      if (half && a == p) break;  // middle row: once
-      T* row = tile + a * ld;
-      T rho = tile[(a + 1) * ld + a];
-      row[a + 1] = O::mul(row[a + 1], rho);
-      for (int b = a + 2; b < N; ++b) {
-        rho = O::mul(rho, tile[b * ld + b - 1]);
-        row[b] = O::mul(row[b], rho);
+    const int a0 = p, a1 = N - 2 - p;
+    const int l0 = N - 1 - a0, l1 = (a1 != a0) ? N - 1 - a1 : 0;
+    int a = a0, b = a0 + 1;
+    T rho = O::one();
+    for (int e = 0; e < l0 + l1; ++e) {
+      if (e == l0) {  // second row of the pair
+        a = a1;
+        b = a1 + 1;
       }
+      const T sub = tile[b * ld + b - 1];
+      rho = (b == a + 1) ? sub : O::mul(rho, sub);
+      T* h = tile + a * ld + b;
+      *h = O::mul(*h, rho);
+      ++b;
     }
   }
   __syncwarp();

@@ -75,16 +75,22 @@ def pad_odd(M):
     return P
 
 
-def stored(name: str):
-    """(value, abs_sum) of a stored oracle case from oracle_values.json."""
+def stored_case(name: str) -> dict:
+    """The record of a stored oracle case (oracle_values.json)."""
     import json
     import os
 
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_values.json")) as f:
         for c in json.load(f)["cases"]:
             if c["name"] == name:
-                return complex(c["re"], c["im"]), float(c["abs_sum"])
+                return c
     raise KeyError(name)
+
+
+def stored(name: str):
+    """(value, abs_sum) of a stored oracle case."""
+    c = stored_case(name)
+    return complex(c["re"], c["im"]), float(c["abs_sum"])
 
 
 def case_matrix(c):
