@@ -311,9 +311,10 @@ int haf_batched_tune(const double* const* As, const int64_t* ns, int64_t count, 
  *   destroy      : stops admitting and publishing work, lets the chunks
  *                  already handed to the GPU finish, then frees everything
  *                  (results not yet collected are lost).
- * The resident kernel exits once no warp has claimed a chunk for idle_us,
- * and the scheduler relaunches it when work arrives; no device wait is
- * unbounded.  create fails with HAF_EINVAL for max_jobs > 65535 or
+ * The resident kernel exits once no warp has claimed a chunk for idle_us
+ * and no claimed chunk is unfinished (or after 3000 x idle_us without a
+ * claim, whatever is in flight), and the scheduler relaunches it when work
+ * arrives; no device wait is unbounded.  create fails with HAF_EINVAL for max_jobs > 65535 or
  * ring_entries < 65536.
  * ---------------------------------------------------------------------- */
 typedef struct haf_server haf_server;

@@ -74,14 +74,16 @@ struct ServerArgs {
   unsigned long long cap[2];          // ring entries
   const unsigned long long* tail[2];  // device: chunks published so far (host copy, after the entries)
   unsigned long long* head;           // device: [kSrvHeadClaim0/1] chunks claimed per ring,
-                                      // [kSrvHeadLast] time of the latest claim, [2..9] diagnostics
+                                      // [kSrvHeadLast] time of the latest claim, [kSrvHeadDone]
+                                      // claimed chunks finished, the rest diagnostics
   unsigned int* stop;                 // device: nonzero makes every warp leave (set by the host's
                                       // copy at shutdown, or by the first warp that finds the
                                       // kernel idle)
   unsigned long long* stats;          // mapped host, diagnostic words (see the server's log)
   const SrvJob* jobs;                 // device job table
   const double* tables;
-  long long idle_ns;                  // the kernel leaves after this long without a claim
+  long long idle_ns;                  // the kernel leaves after this long without a claim and
+                                      // with no claimed chunk unfinished
 };
 constexpr int kMaxSmemPerBlock = 232448;  // 227 KiB opt-in on sm_100/sm_103
 // Shared memory owned by each warp when a CTA has `wpb` warps.
@@ -97,7 +99,11 @@ constexpr int kSrvSmallBytes = warp_bytes_for(8);
 constexpr int kSrvBigBytes = warp_bytes_for(4);
 constexpr int kSrvSmemBytes = kSrvSmallWarps * kSrvSmallBytes + kSrvBigBytes;
 static_assert(kSrvSmemBytes <= kMaxSmemPerBlock, "server CTA shared memory");
-constexpr int kSrvHeadClaim0 = 0, kSrvHeadLast = 1, kSrvHeadClaim1 = 10;
+constexpr int kSrvHeadClaim0 = 0, kSrvHeadLast = 1, kSrvHeadDone = 7, kSrvHeadClaim1 = 10;
+// A quiet spell this many times idle_ns ends the kernel even with chunks
+// still counted in flight (a bound on the idle wait; the warps then finish
+// what they hold, claim nothing more, and the host relaunches).
+constexpr long long kSrvQuietCap = 3000;
 
 // Precision of the bulk steps (gather, Householder, loop moments, La Budde).
 // The power series, f(Z) and the subset sum are FP64 in both modes.

@@ -1082,6 +1082,12 @@ __global__ void __launch_bounds__(32 * kSrvWarps, 1) server_kernel(ServerArgs a)
     if (lane == 0) {
       unsigned int nap = 256;
       for (;;) {
+        // once the stop flag is up no warp claims anything more, so the
+        // kernel ends when the chunks already claimed are done
+        if (ld_relaxed_gpu(a.stop) != 0u) {
+          status = 2;
+          break;
+        }
         // try the rings this warp serves, in order
         for (int q = big ? 0 : 1; q < 2 && status == 0; ++q) {
           const int rg = big ? 1 - q : 0;  // big warp: ring 1, then ring 0
@@ -1109,15 +1115,22 @@ __global__ void __launch_bounds__(32 * kSrvWarps, 1) server_kernel(ServerArgs a)
         }
         if (status) break;
         atomicAdd(a.head + 2, 1ull);  // diagnostic: idle polls
-        if (ld_relaxed_gpu(a.stop) != 0u) {
-          status = 2;
-          break;
-        }
-        const long long now = globaltimer();
-        if (now - max(started, *last_claim) > a.idle_ns) {
-          atomicExch(a.stop, 1u);
-          status = 2;
-          break;
+        const long long quiet = globaltimer() - max(started, *last_claim);
+        if (quiet > a.idle_ns) {
+          // idle: no claim for idle_ns, and every claimed chunk finished (the
+          // finished count is read first, so a zero difference means none was
+          // in flight when it was read and none claimed since).  While a warp
+          // still works on a long chunk the others keep polling: a stop then
+          // would strand the published entries behind a kernel that runs on
+          // with only the busy warps.
+          const unsigned long long fin = atomicAdd(a.head + kSrvHeadDone, 0ull);
+          const unsigned long long cl =
+              atomicAdd(a.head + kSrvHeadClaim0, 0ull) + atomicAdd(a.head + kSrvHeadClaim1, 0ull);
+          if (cl == fin || quiet / kSrvQuietCap > a.idle_ns) {
+            atomicExch(a.stop, 1u);
+            status = 2;
+            break;
+          }
         }
         __nanosleep(nap);
         nap = min(nap * 2u, 32768u);
@@ -1152,7 +1165,10 @@ __global__ void __launch_bounds__(32 * kSrvWarps, 1) server_kernel(ServerArgs a)
     if (ch.tag != (uint16_t)(sj.gen & 0xffffu)) {
       // a descriptor that does not belong to the job now in its slot: count
       // it and leave the job's counters alone (diagnostic; never expected)
-      if (lane == 0) st_relaxed_sys(a.stats + 3, atomicAdd(a.head + 5, 1ull) + 1);
+      if (lane == 0) {
+        st_relaxed_sys(a.stats + 3, atomicAdd(a.head + 5, 1ull) + 1);
+        atomicAdd(a.head + kSrvHeadDone, 1ull);
+      }
       continue;
     }
     const long long tc0 = globaltimer();
@@ -1205,6 +1221,7 @@ __global__ void __launch_bounds__(32 * kSrvWarps, 1) server_kernel(ServerArgs a)
         st_release_sys(sj.flag, sj.gen);
       }
     }
+    if (lane == 0) atomicAdd(a.head + kSrvHeadDone, 1ull);  // this claim is finished
   }
 }
 
