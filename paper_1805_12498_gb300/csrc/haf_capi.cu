@@ -164,10 +164,10 @@ int build_plan(const std::vector<JobSpec>& jobs, int sms, const PlanCfg& pc, Pla
       const int N = 2 * c.m, S = 32 / c.cfg.G;
       const double per = std::pow((double)N, 3);
       const double target = std::max(1.0, work[c.wpb] / ((double)sms * c.wpb * pc.chunks_per_warp));
-      // a cap on chunk work, but never more than 65,536 chunks per job
+      // a cap on chunk work, but never more than js.max_chunks chunks per job
       double tj = target;
       if (js.max_chunk_units > 0)
-        tj = std::max(std::min(target, js.max_chunk_units), job_total / (double)js.nparts / 65536.0);
+        tj = std::max(std::min(target, js.max_chunk_units), job_total / (double)js.nparts / js.max_chunks);
       uint64_t csz = (uint64_t)std::ceil(tj / per / S) * S;
       csz = std::max<uint64_t>(csz, (uint64_t)S);
       csz = std::min<uint64_t>(csz, (uint64_t)1 << 30);

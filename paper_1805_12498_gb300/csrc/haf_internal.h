@@ -165,7 +165,8 @@ struct JobSpec {
   int is_real;
   int64_t part = 0;  // this job covers part `part` of `nparts` of every size class
   int64_t nparts = 1;
-  double max_chunk_units = 0;  // cap on a chunk's work in N^3 units (0: none)
+  double max_chunk_units = 0;  // cap on a chunk's work in N^3 units (0: none) ...
+  double max_chunks = 65536;   // ... but never more chunks than this per job (part)
   int prec = kPrecF64;         // all jobs of one plan share is_real and prec
 };
 // Launch shape of a plan: warps per CTA (4, 8 or 16; size classes whose

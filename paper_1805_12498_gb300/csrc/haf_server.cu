@@ -72,6 +72,7 @@ struct JobRec {
   size_t off = 0, bytes = 0;  // arena region
   std::vector<Chunk> chunks[2];  // per ring (0: small tiles, 1: large), publication order
   size_t next_pub[2] = {0, 0};
+  double pub_units = 0;      // work published so far (both rings), for the publication order
   int64_t subsets = 0;
   bool all_published() const { return next_pub[0] >= chunks[0].size() && next_pub[1] >= chunks[1].size(); }
   cudaEvent_t uploaded = nullptr;
@@ -143,6 +144,12 @@ struct haf_server {
     uint64_t cap = 0;
     uint64_t published = 0;
     uint64_t claimed = 0;    // a lower bound, from the read-back
+    std::vector<double> cum; // cum[i % cap] = work of entries 0..i (N^3 units)
+    double pub_units = 0;    // work of all published entries
+    double queued_units() const {  // published, not (known to be) claimed
+      const uint64_t c = std::min(claimed, published);
+      return pub_units - (c ? cum[(c - 1) % cap] : 0.0);
+    }
   } ring[2];
   unsigned long long* tail_dev = nullptr;  // ring r's count at tail_dev[16 r]
   unsigned long long* tail_src = nullptr;  // pinned rotating sources of the count copies
@@ -203,11 +210,22 @@ void prep_host(const JobRec& j, char* dst_at, char* dst_diag) {
 
 // Server jobs are cut into chunks of about cfg.chunk_us of one warp's time
 // (a warp retires roughly 75 N^3 units per microsecond at the FP64 rate), so
-// a newly admitted small job waits at most about one chunk for a warp.
+// a newly admitted small job waits at most about one chunk for a warp.  Up
+// to kSrvMaxChunks chunks per job: at n = 52 that keeps a chunk near 60 ms
+// of a warp (40-byte partial per chunk, 10 MB for such a job).
+constexpr double kSrvUnitsPerUs = 75.0;
+constexpr double kSrvMaxChunks = 262144.0;
 JobSpec server_spec(const haf_server* s, int n, int loops) {
   JobSpec js{n, loops, 0};
-  js.max_chunk_units = 75.0 * (double)s->cfg.chunk_us;
+  js.max_chunk_units = kSrvUnitsPerUs * (double)s->cfg.chunk_us;
+  js.max_chunks = kSrvMaxChunks;
   return js;
+}
+
+// Work of a chunk in N^3 units (the planner's measure).
+double chunk_units(const Chunk& c) {
+  const double N = 2.0 * c.m;
+  return (double)c.count * N * N * N;
 }
 
 // Server plans: 8 warps per CTA for the tiles that fit the small slices,
@@ -248,6 +266,7 @@ bool admit_one(haf_server* s) {
     j.chunks[r].clear();
     j.next_pub[r] = 0;
   }
+  j.pub_units = 0;
   for (const PlanSeg& sg : p.segs) {
     const int r = sg.wpb == 8 ? 0 : 1;  // 8-warp slices: small ring; 4-warp slices: large ring
     for (int q = sg.begin; q < sg.end; ++q) {
@@ -347,12 +366,19 @@ void scheduler(haf_server* s) {
       JobRec& j = *kv.second;
       if (j.state == kUploading && cudaEventQuery(j.uploaded) == cudaSuccess) j.state = kReady;
     }
-    // 4. publish round robin, with bounded depth and ring space.  The count
-    //    of claimed chunks comes from a copy of the device counter (a lower
-    //    bound, refreshed every pass).  A ring slot may be rewritten once its
-    //    entry has been claimed and read: a warp reads the entry it claimed
-    //    before it claims another, so at most one claimed-but-unread entry
-    //    per warp exists, which the margin covers.
+    // 4. publish, least published work first, with bounded depth and ring
+    //    space.  The count of claimed chunks comes from a copy of the device
+    //    counter (a lower bound, refreshed every pass).  A ring slot may be
+    //    rewritten once its entry has been claimed and read: a warp reads the
+    //    entry it claimed before it claims another, so at most one
+    //    claimed-but-unread entry per warp exists, which the margin covers.
+    //    Order: the jobs with the least work published so far go first, a
+    //    burst of chunks each in turn, so a new job's chunks enter the ring
+    //    ahead of the rest of a long job's.  Depth: at most one queued
+    //    (published, unclaimed) chunk per warp that serves the ring, and at
+    //    most about two target-sized chunks of work per such warp, so a new
+    //    entry waits behind little work even when a long job's chunks are
+    //    large.
     if (s->claimed_pending && cudaEventQuery(s->claimed_ev) == cudaSuccess) {
       s->ring[0].claimed = std::max<uint64_t>(s->ring[0].claimed, s->claimed_h[kSrvHeadClaim0]);
       s->ring[1].claimed = std::max<uint64_t>(s->ring[1].claimed, s->claimed_h[kSrvHeadClaim1]);
@@ -364,24 +390,36 @@ void scheduler(haf_server* s) {
           cudaEventRecord(s->claimed_ev, s->status) == cudaSuccess)
         s->claimed_pending = true;
     }
+    std::vector<JobRec*> order;
+    for (auto& kv : s->jobs)
+      if (kv.second->state == kReady && !kv.second->all_published()) order.push_back(kv.second.get());
+    std::stable_sort(order.begin(), order.end(),
+                     [](const JobRec* a, const JobRec* b) { return a->pub_units < b->pub_units; });
     for (int r = 0; r < 2; ++r) {
       haf_server::Ring& R = s->ring[r];
-      // queue depth: about one chunk per warp that serves the ring
       const uint64_t claimed = std::min<uint64_t>(R.claimed, R.published);
       const uint64_t margin = 4ull * ring_warps[r];
       const uint64_t lim = (claimed > margin ? claimed - margin : 0) + R.cap;
+      const double work_cap = 2.0 * kSrvUnitsPerUs * (double)s->cfg.chunk_us * (double)ring_warps[r];
+      double queued = R.queued_units();
       bool progress = true;
       const uint64_t before = R.published;
       while (progress) {
         progress = false;
-        for (auto& kv : s->jobs) {
-          JobRec& j = *kv.second;
-          if (j.state != kReady || j.next_pub[r] >= j.chunks[r].size()) continue;
-          if (R.published - claimed >= ring_warps[r] || R.published >= lim) break;
+        for (JobRec* jp : order) {
+          JobRec& j = *jp;
+          if (j.next_pub[r] >= j.chunks[r].size()) continue;
+          if (R.published - claimed >= ring_warps[r] || R.published >= lim || queued >= work_cap) break;
           const size_t burst = 4;
           for (size_t q = 0; q < burst && j.next_pub[r] < j.chunks[r].size() && R.published < lim; ++q) {
-            R.stage[R.published % R.cap] = j.chunks[r][j.next_pub[r]++];
+            const Chunk& c = j.chunks[r][j.next_pub[r]++];
+            const double u = chunk_units(c);
+            R.stage[R.published % R.cap] = c;
+            R.pub_units += u;
+            R.cum[R.published % R.cap] = R.pub_units;
             ++R.published;
+            queued += u;
+            j.pub_units += u;
             progress = true;
           }
         }
@@ -490,7 +528,10 @@ int haf_server_create(const haf_server_cfg* cfg, haf_server** out) {
   for (int k = 1; k < 128; ++k) tab[128 + k] = 1.0 / k;
   SRV_CUDA(cudaMalloc(&s->tables, 256 * sizeof(double)));
   SRV_CUDA(cudaMemcpy(s->tables, tab.data(), 256 * sizeof(double), cudaMemcpyHostToDevice));
-  for (int r = 0; r < 2; ++r) s->ring[r].cap = (uint64_t)s->cfg.ring_entries;
+  for (int r = 0; r < 2; ++r) {
+    s->ring[r].cap = (uint64_t)s->cfg.ring_entries;
+    s->ring[r].cum.assign(s->ring[r].cap, 0.0);
+  }
   SRV_CUDA(cudaStreamCreateWithFlags(&s->pub, cudaStreamNonBlocking));
   SRV_CUDA(cudaStreamCreateWithFlags(&s->status, cudaStreamNonBlocking));
   SRV_CUDA(cudaEventCreateWithFlags(&s->claimed_ev, cudaEventDisableTiming));
