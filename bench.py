@@ -230,33 +230,73 @@ def precision_leg(seed: int, value48=None):
 
 
 def lowrank_leg(seed: int):
-    """Low-rank hafnian (App. C expansion) at n = 56 for ranks 4, 6, 8:
-    seconds per hafnian and monomials per second (the expansion processes
-    C(k+r-1, r-1) monomials at each degree k = 1..n)."""
+    """Low-rank hafnian (App. C expansion) at n = 56 for ranks 4, 6, 8.  The
+    step kernels are bound by the FP64 pipe (5 DFMA per term), so the
+    roofline is against the DFMA probe.  The device leg times
+    haf_lowrank_launch (G, workspace and result in device
+    memory; the n + 3 launches of one expansion) with CUDA events on the
+    launching stream; the host leg times the synchronous haf_lowrank call
+    (G from host memory, the result read back, the workspace allocated and
+    freed inside the call above 256 MB).  The expansion processes
+    C(k+r-1, r-1) monomials at each degree k = 1..n."""
     import math
+
+    import torch
 
     import paper_1805_12498_gb300 as hg
     from paper_1805_12498_gb300 import inputs
 
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    peak_tflops, _ = hg.fp64_peak()
     rows = []
     for n, r in ((56, 4), (56, 6), (56, 8)):
         g = inputs.rng(seed + 100 * r + n)
         G = (g.normal(size=(n, r)) + 1j * g.normal(size=(n, r))) / np.sqrt(2 * r)
-        hg.haf_lowrank(G)
+        ws = hg.lowrank_workspace_bytes(n, r)
+        work = torch.empty(ws // 8 + 64, dtype=torch.float64, device=dev)
+        wptr = (work.data_ptr() + 255) // 256 * 256
+        dG = torch.from_numpy(G.view(np.float64).copy()).to(dev)
+        out = torch.zeros(5, dtype=torch.float64, device=dev)
+
+        def launch():
+            hg.haf_lowrank_launch(dG.data_ptr(), n, r, out.data_ptr(), wptr, ws, stream.cuda_stream)
+
+        launch()
+        torch.cuda.synchronize(dev)
+        reps = 3
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            launch()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        rec = out.cpu().numpy()
+        del work
+        torch.cuda.empty_cache()
         t = time.perf_counter()
         a = hg.haf_lowrank(G)
         dt = time.perf_counter() - t
+        same = complex(rec[0] + rec[2], rec[1] + rec[3]) == a.value
         mono = sum(math.comb(k + r - 1, r - 1) for k in range(1, n + 1))
+        # algorithmic work: at degree k every monomial e takes one term per
+        # j with e_j >= 1, i.e. r * C(k-1+r-1, r-1) terms in all; a term is a
+        # complex multiply-add and a real one (|g| recurrence): 10 flops
+        flops = 10.0 * r * math.comb(n - 1 + r, r)
         # minimal traffic: every degree-k array (24 B per monomial: value + abs) written once, read once
         traffic = 2 * 24 * mono
-        rows.append({"n": n, "r": r, "s": dt, "monomials_per_s": mono / dt, "abs_sum": a.abs_sum,
-                     "roofline": {"bound": "hbm", "achieved": traffic / dt / 1e9, "peak": hbm_peak_gbs(),
-                                  "unit": "GB/s", "frac": traffic / dt / 1e9 / hbm_peak_gbs(),
-                                  "note": "algorithmic bytes = 48 B per monomial update (its degree array "
-                                          "written once and read once); host-clock time; peak = "
-                                          "MEASURED_PEAKS.json hbm_gbs (of measured)"}})
-    return {"workload": "haf(G G^T), G complex Gaussian n x r, App. C expansion on the GPU (host clock, "
-                        "synchronous calls)", "rows": rows}
+        tf = flops / (ms / 1e3) / 1e12
+        rows.append({"n": n, "r": r, "ms_device": ms, "monomials_per_s": mono / (ms / 1e3),
+                     "s_host_call": dt, "host_equals_device": bool(same), "abs_sum": a.abs_sum,
+                     "hbm_alg_gbs": traffic / (ms / 1e3) / 1e9,
+                     "roofline": {"bound": "alu", "achieved": tf, "peak": peak_tflops, "unit": "TFLOP/s",
+                                  "frac": tf / peak_tflops,
+                                  "note": "FP64 pipe: 10 flops (5 DFMA) per term, r * C(n-1+r, r) terms per "
+                                          "expansion, / CUDA-event time of the n + 3 launches; peak = DFMA probe "
+                                          "measured in this run (of measured). hbm_alg_gbs = 48 B per monomial "
+                                          "(each degree array written once, read once) over the same time"}})
+    return {"workload": "haf(G G^T), G complex Gaussian n x r, App. C expansion on the GPU", "rows": rows}
 
 
 def hbm_peak_gbs() -> float:
@@ -417,6 +457,10 @@ def summary_fields(line: dict) -> dict:
         out["serving_p99_ms"] = sv["p99_ms"]
         out["one_launch_fifo_p50_ms"] = sv["one_launch_fifo_p50_ms"]
         out["one_launch_fifo_p99_ms"] = sv["one_launch_fifo_p99_ms"]
+    if "lowrank" in line:
+        last = line["lowrank"]["rows"][-1]
+        out[f"lowrank_r{last['r']}_ms"] = last["ms_device"]
+        out[f"lowrank_r{last['r']}_fp64_frac"] = last["roofline"]["frac"]
     return out
 
 
@@ -513,6 +557,7 @@ def main():
                     help="largest n of the serving mix (n even in [8, nmax], P(n) ~ 2^(-n/8))")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32-vs-FP64 precision leg")
     ap.add_argument("--no-lhaf", action="store_true", help="skip the loop-hafnian leg")
+    ap.add_argument("--no-lowrank", action="store_true", help="skip the low-rank (App. C) leg")
     ap.add_argument("--shard", action="store_true",
                     help="split ONE hafnian of size --n over the ranks (strong scaling) instead of one per rank")
     args = ap.parse_args()
@@ -633,8 +678,9 @@ def main():
             line["batched"] = batched_leg(args.gbs_batch, args.seed)
         if args.serve_requests > 0 and world == 1:
             line["serving"] = serving_leg(args.serve_requests, args.serve_nmax, args.seed)
-        if not args.no_precision and world == 1:
+        if not args.no_lowrank and world == 1:
             line["lowrank"] = lowrank_leg(args.seed)
+        if not args.no_precision and world == 1:
             line["precision"] = precision_leg(args.seed, (complex(res[0] + res[2], res[1] + res[3]), float(res[4]),
                                                           ms_step * 1e-3))
         if not args.no_cpu_baseline and world == 1:

@@ -254,6 +254,25 @@ int haf_terms(const double* A, int64_t n, uint32_t flags, const uint64_t* masks,
 #define HAF_LOWRANK_MAX_R 16
 int haf_lowrank_c128(const double* G, int64_t n, int64_t r, double* out, haf_info* info);
 
+/* Device-pointer form of the low-rank hafnian (App. C), like haf_launch:
+ *   dG        : device pointer, G complex128 row-major n x r
+ *   d_out     : device pointer to 5 doubles written as
+ *               {re_hi, im_hi, re_lo, im_lo, abs_sum}
+ *   d_work    : device workspace of at least haf_lowrank_workspace_bytes(n,
+ *               r) bytes, 256-byte aligned, not shared with a concurrent
+ *               call (it holds the two largest coefficient arrays: 48 bytes
+ *               per degree-n monomial, plus small tables)
+ *   stream    : cudaStream_t (NULL = legacy default stream)
+ * The call only enqueues work (n + 3 kernel launches) and returns before the
+ * result is ready.  n must be even, 2..HAF_LOWRANK_MAX_N (the host entry
+ * point handles 0 and odd n), 1 <= r <= HAF_LOWRANK_MAX_R; HAF_EINVAL
+ * otherwise or for a misaligned workspace, HAF_ESMALL if ws_bytes is too
+ * small, HAF_ENOMEM if C(n+r-1, r-1) >= 2^40.  haf_lowrank_workspace_bytes
+ * returns 0 for sizes that the launch rejects. */
+size_t haf_lowrank_workspace_bytes(int64_t n, int64_t r);
+int haf_lowrank_launch(const double* dG, int64_t n, int64_t r, double* d_out, void* d_work, size_t ws_bytes,
+                       void* stream);
+
 /* ------------------------------------------------------------------------
  * Autotuner (no counterpart in the paper).  The launch shape of a plan is
  * the number of warps per CTA (4, 8 or 16: the shared-memory slice of each

@@ -26,7 +26,7 @@ from ._native import (HAF_FLAG_FP32, HAF_FLAG_LOOPS, HAF_FLAG_REAL, HAF_MAX_N, H
 
 __all__ = ["haf", "lhaf", "haf_info", "haf_batched", "haf_terms", "workspace_bytes",
            "haf_launch", "haf_launch_noalloc", "haf_part", "part_subsets", "combine", "Server", "fp64_peak", "tune",
-           "tune_set", "batched_tune", "haf_lowrank", "HafError", "HafAccuracyError", "HAF_MAX_N",
+           "tune_set", "batched_tune", "haf_lowrank", "haf_lowrank_launch", "lowrank_workspace_bytes", "HafError", "HafAccuracyError", "HAF_MAX_N",
            "HAF_FP32_MAX_N", "HAF_FP32_REL_TOL", "HAF_FP64_REL_TOL", "HAF_FP32_MAX_REL_ERR"]
 
 # Accuracy constants of include/hafnian_gb300.h: the error per unit of
@@ -274,6 +274,22 @@ def haf_lowrank(G) -> Info:
     _native.check(_native.lib().haf_lowrank_c128(G.ctypes.data_as(_native._DP), G.shape[0], G.shape[1],
                                                  out.ctypes.data_as(_native._DP), ctypes.byref(info)))
     return _info(complex(out[0], out[1]), info)
+
+
+def lowrank_workspace_bytes(n: int, r: int) -> int:
+    """Device workspace of ``haf_lowrank_launch`` for an n x r matrix G."""
+    b = _native.lib().haf_lowrank_workspace_bytes(n, r)
+    if b == 0:
+        raise HafError(_native.HAF_EINVAL, f"no low-rank workspace size for n={n}, r={r}")
+    return int(b)
+
+
+def haf_lowrank_launch(dG_ptr: int, n: int, r: int, d_out_ptr: int, d_work_ptr: int, ws_bytes: int,
+                       stream_ptr: int = 0) -> None:
+    """Enqueue the App. C expansion for G (complex128, row-major n x r) in
+    device memory; the 5-double record {re_hi, im_hi, re_lo, im_lo,
+    abs_sum} lands at d_out_ptr when the stream reaches it."""
+    _native.check(_native.lib().haf_lowrank_launch(dG_ptr, n, r, d_out_ptr, d_work_ptr, ws_bytes, stream_ptr))
 
 
 def tune(n: int, loops: bool = False, real: bool = False, precision: str = "fp64", reps: int = 1) -> dict:

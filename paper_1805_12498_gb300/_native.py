@@ -104,6 +104,11 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         L.haf_terms.restype = ctypes.c_int
         L.haf_lowrank_c128.argtypes = [_DP, ctypes.c_int64, ctypes.c_int64, _DP, ctypes.POINTER(HafInfo)]
         L.haf_lowrank_c128.restype = ctypes.c_int
+        L.haf_lowrank_workspace_bytes.argtypes = [ctypes.c_int64, ctypes.c_int64]
+        L.haf_lowrank_workspace_bytes.restype = ctypes.c_size_t
+        L.haf_lowrank_launch.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+        L.haf_lowrank_launch.restype = ctypes.c_int
         L.haf_eval.argtypes = [_DP, ctypes.c_int64, ctypes.c_uint32, _DP, ctypes.POINTER(HafInfo)]
         L.haf_eval.restype = ctypes.c_int
         L.haf_batched.argtypes = [ctypes.POINTER(_DP), _I64P, ctypes.c_int64, ctypes.c_uint32, _DP,

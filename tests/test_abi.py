@@ -1,6 +1,7 @@
 """The C-ABI library builds, loads and exports every function that
 include/*.h declares.  No compute calls (this runs without a GPU)."""
 import ctypes
+import math
 import glob
 import os
 import re
@@ -27,7 +28,8 @@ def test_header_declares_entry_points():
                  "lhaf_c128_batched", "haf_launch", "haf_workspace_bytes", "haf_terms_c128",
                  "haf_eval", "haf_batched", "haf_terms", "haf_tune", "haf_tune_set", "haf_batched_tune",
                  "haf_server_create", "haf_server_submit", "haf_server_poll", "haf_server_destroy",
-                 "haf_part", "haf_combine", "haf_launch_noalloc", "haf_lowrank_c128"):
+                 "haf_part", "haf_combine", "haf_launch_noalloc", "haf_lowrank_c128",
+                 "haf_lowrank_workspace_bytes", "haf_lowrank_launch"):
         assert must in names
 
 
@@ -66,6 +68,17 @@ def test_bad_arguments_fail_without_gpu_work():
     assert L.haf_lowrank_c128(None, 4, 2, out, None) == _native.HAF_EINVAL
     assert L.haf_lowrank_c128(A, 4, 0, out, None) == _native.HAF_EINVAL
     assert L.haf_lowrank_c128(A, 4, 17, out, None) == _native.HAF_EINVAL
+    # device-pointer form: argument checks come before any CUDA call (the
+    # pointer values below are never dereferenced)
+    assert L.haf_lowrank_workspace_bytes(5, 2) == 0 and L.haf_lowrank_workspace_bytes(8, 0) == 0
+    assert L.haf_lowrank_workspace_bytes(130, 2) == 0 and L.haf_lowrank_workspace_bytes(8, 17) == 0
+    for nn, rr in ((2, 1), (8, 3), (56, 8)):
+        assert L.haf_lowrank_workspace_bytes(nn, rr) >= 48 * math.comb(nn + rr - 1, rr - 1)
+    assert L.haf_lowrank_launch(None, 4, 2, 256, 256, 1 << 20, None) == _native.HAF_EINVAL
+    assert L.haf_lowrank_launch(256, 5, 2, 256, 256, 1 << 20, None) == _native.HAF_EINVAL
+    assert L.haf_lowrank_launch(256, 4, 0, 256, 256, 1 << 20, None) == _native.HAF_EINVAL
+    assert L.haf_lowrank_launch(256, 4, 2, 256, 8, 1 << 20, None) == _native.HAF_EINVAL  # misaligned
+    assert L.haf_lowrank_launch(256, 8, 3, 256, 256, 64, None) == _native.HAF_ESMALL
     assert L.haf_tune(16, 1 << 7, 1, ctypes.byref(r)) == _native.HAF_EINVAL
 
 
