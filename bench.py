@@ -64,13 +64,29 @@ def alg_flops(n: int) -> float:
     return (44.0 / 3.0) * (2 ** h) * h * h * (h + 3)
 
 
+def lhaf_extra_flops(N: int, h: int) -> float:
+    """FP64 flops that a loop-hafnian summand adds to the hafnian's for one
+    subset of size N = 2|Z| (Sec. 3.3, q(lambda, B, v)), as the kernels do
+    it (a complex multiply-add is 8 flops):
+      - the Krylov-start reflector of length N applied to B from both sides:
+        4 N^2 multiply-adds;
+      - every reflector applied to the vector a: about N^2 multiply-adds;
+      - the moments u_k = a H^(k-1) b for k = 2..K, K = min(N, h): the
+        Hessenberg product on a vector supported on its first k-1 entries,
+        (k-1)(k+2)/2 multiply-adds, and the dot with a, k more;
+      - for N < h, Cayley-Hamilton's continuation to u_h: N per moment."""
+    K = min(N, h)
+    mom = sum((k - 1) * (k + 2) / 2.0 + k for k in range(2, K + 1))
+    tail = (h - N) * N if N < h else 0
+    return 8.0 * (4 * N * N + N * N + mom + tail)
+
+
 def alg_flops_lhaf(n: int) -> float:
-    """Algorithmic FP64 flops of one loop hafnian: the hafnian's count plus,
-    per subset, the loop moments' 8 ((h-1) N^2 / 2 + 2 N^2) (N = 2|Z|)."""
+    """Algorithmic FP64 flops of one loop hafnian: the hafnian's count plus
+    lhaf_extra_flops summed over the subsets."""
     from math import comb
     h = n // 2
-    extra = sum(comb(h, m) * 8.0 * ((h - 1) * (2 * m) ** 2 / 2.0 + 2.0 * (2 * m) ** 2) for m in range(1, h + 1))
-    return alg_flops(n) + extra
+    return alg_flops(n) + sum(comb(h, m) * lhaf_extra_flops(2 * m, h) for m in range(1, h + 1))
 
 
 class ClockSampler:
@@ -435,7 +451,8 @@ def lhaf_leg(hg, torch, dA, n, stream, flush, steps: int, peak: float):
     return {"workload": f"lhaf of the same {n}x{n} matrix (diagonal kept), 2^{n // 2} subset terms",
             "ms_per_step": ms, "steps": steps, "subset_terms_per_s": 2 ** (n // 2) / (ms * 1e-3),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "note": "haf flops + per subset 8 ((h-1) N^2/2 + 2 N^2) for the loop moments; "
+                         "note": "haf flops + per subset the Krylov-start reflector, the reflectors on a, "
+                                 "the sparse moments and the Cayley-Hamilton tail (lhaf_extra_flops); "
                                  "CUDA-event time; peak = DFMA probe (of measured)"}}
 
 

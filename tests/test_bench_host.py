@@ -28,6 +28,29 @@ def test_alg_flops_at_the_benchmark_size():
     assert bench.alg_flops(48) == pytest.approx(3.8268e12, rel=1e-4)
 
 
+@pytest.mark.parametrize("N,h", [(2, 1), (4, 6), (10, 8), (24, 24), (48, 24)])
+def test_lhaf_extra_flops_counts_the_kernels_loops(N, h):
+    """The moments' count, by walking the loop structure the kernel runs:
+    at step k the rows 0..k-1 of H times a vector supported on its first
+    k-1 entries (row 0: k-1 entries, row i >= 1: k-i), then the dot with a;
+    Cayley-Hamilton past N; the Krylov-start reflector both sides (4 N^2)
+    and the reflectors on a (N^2)."""
+    K = min(N, h)
+    macs = 4 * N * N + N * N
+    for k in range(2, K + 1):
+        macs += sum(k - 1 if i == 0 else k - i for i in range(k)) + k
+    for k in range(N + 1, h + 1):
+        macs += N
+    assert bench.lhaf_extra_flops(N, h) == pytest.approx(8 * macs, rel=1e-15)
+
+
+def test_alg_flops_lhaf_sums_the_subsets():
+    n, h = 12, 6
+    want = bench.alg_flops(n) + sum(comb(h, m) * bench.lhaf_extra_flops(2 * m, h) for m in range(1, h + 1))
+    assert bench.alg_flops_lhaf(n) == pytest.approx(want, rel=1e-15)
+    assert 1.15 < bench.alg_flops_lhaf(48) / bench.alg_flops(48) < 1.25
+
+
 def test_clock_summary():
     s = bench.ClockSampler(0)
     s.samples = [["2070", "2070", "900.1", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
