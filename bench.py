@@ -23,8 +23,9 @@ Printed (rank 0, one JSON line):
           synchronous call per request (capacity and FIFO latency);
   precision  the FP32-bulk mode against FP64 at n = 40 and 48 (error
           relative to sum |f(Z)| and to |haf|, speed-up);
-  lowrank  the App. C expansion at n = 56, r = 4, 6, 8.
-The last five legs run at N = 1 only.
+  lowrank  the App. C expansion at n = 56, r = 4, 6, 8;
+  sweep  complex and real haf and lhaf at n = 24, 28, ..., 52, one call each.
+The last six legs run at N = 1 only; --no-<leg> flags skip them.
 Multi-GPU (torchrun): each rank computes its own hafnian (independent
 problems, no collective on the data path): weak scaling.
 ``--impl reference``: the oracle itself, timed on the host cores (rank 0).
@@ -157,6 +158,57 @@ def cpu_baseline(n: int, seed: int, budget_s: float = 12.0):
     return {"value": count / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{count} uniformly random subsets of the n={n} seeded complex Gaussian "
                       f"matrix, binary128 trace-power summands, {dt:.1f} s"}
+
+
+def sweep_leg(seed: int, sizes=(24, 28, 32, 36, 40, 44, 48, 52)):
+    """The single-hafnian size sweep: one seeded matrix per size, complex
+    (A = (G + G^T)/2, re, im ~ N(0, 1/2)) and real (N(0, 1) entries), haf
+    and lhaf, each timed once with CUDA events on the launching stream
+    through haf_launch (device-resident input; one untimed warm-up call
+    below n = 40, where plan building would show).  The FP64 fraction uses
+    the hafnian's and loop hafnian's flop counts, a quarter of them for real
+    input (a real multiply-add is 2 flops, a complex one 8)."""
+    import torch
+
+    import paper_1805_12498_gb300 as hg
+    from paper_1805_12498_gb300 import inputs
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    peak, _ = hg.fp64_peak()
+    rows = []
+    for n in sizes:
+        for real in (False, True):
+            A = inputs.real_gaussian_symmetric(n, seed + n) if real else inputs.complex_gaussian_symmetric(n, seed + n)
+            dA = torch.from_numpy(np.ascontiguousarray(A).view(np.float64).copy()).to(dev)
+            for loops in (False, True):
+                ws = hg.workspace_bytes(n, loops=loops, real=real)
+                work = torch.empty(ws // 8 + 64, dtype=torch.float64, device=dev)
+                wptr = (work.data_ptr() + 255) // 256 * 256
+                out = torch.zeros(5, dtype=torch.float64, device=dev)
+
+                def launch():
+                    hg.haf_launch(dA.data_ptr(), n, out.data_ptr(), wptr, ws, stream.cuda_stream, loops=loops,
+                                  real=real)
+
+                if n < 40:
+                    launch()
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                launch()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms = e0.elapsed_time(e1)
+                flops = (alg_flops_lhaf(n) if loops else alg_flops(n)) / (4.0 if real else 1.0)
+                rec = out.cpu().numpy()
+                rows.append({"n": n, "dtype": "f64" if real else "c128", "loops": loops, "ms": ms,
+                             "subset_terms_per_s": 2 ** (n // 2) / (ms * 1e-3),
+                             "fp64_frac": flops / (ms * 1e-3) / 1e12 / peak, "abs_sum": float(rec[4])})
+                del work
+    return {"workload": "one seeded complex and one real Gaussian symmetric matrix per size n = "
+                        + ",".join(str(n) for n in sizes) + "; haf and lhaf; haf_launch, CUDA events, one call each",
+            "peak_tflops": peak, "rows": rows}
 
 
 def batched_leg(count: int, seed: int, reps: int = 3):
@@ -474,6 +526,10 @@ def summary_fields(line: dict) -> dict:
         out["serving_p99_ms"] = sv["p99_ms"]
         out["one_launch_fifo_p50_ms"] = sv["one_launch_fifo_p50_ms"]
         out["one_launch_fifo_p99_ms"] = sv["one_launch_fifo_p99_ms"]
+    if "sweep" in line:
+        for row in line["sweep"]["rows"]:
+            if row["n"] == max(r["n"] for r in line["sweep"]["rows"]) and row["dtype"] == "c128":
+                out[f"sweep_c128_n{row['n']}_{'lhaf' if row['loops'] else 'haf'}_s"] = row["ms"] / 1e3
     if "lowrank" in line:
         last = line["lowrank"]["rows"][-1]
         out[f"lowrank_r{last['r']}_ms"] = last["ms_device"]
@@ -575,6 +631,9 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32-vs-FP64 precision leg")
     ap.add_argument("--no-lhaf", action="store_true", help="skip the loop-hafnian leg")
     ap.add_argument("--no-lowrank", action="store_true", help="skip the low-rank (App. C) leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the n = 24..52 size sweep")
+    ap.add_argument("--sweep-sizes", default="24,28,32,36,40,44,48,52",
+                    help="sizes of the sweep leg (n = 56 adds about six minutes)")
     ap.add_argument("--shard", action="store_true",
                     help="split ONE hafnian of size --n over the ranks (strong scaling) instead of one per rank")
     args = ap.parse_args()
@@ -697,6 +756,8 @@ def main():
             line["serving"] = serving_leg(args.serve_requests, args.serve_nmax, args.seed)
         if not args.no_lowrank and world == 1:
             line["lowrank"] = lowrank_leg(args.seed)
+        if not args.no_sweep and world == 1:
+            line["sweep"] = sweep_leg(args.seed, tuple(int(x) for x in args.sweep_sizes.split(",")))
         if not args.no_precision and world == 1:
             line["precision"] = precision_leg(args.seed, (complex(res[0] + res[2], res[1] + res[3]), float(res[4]),
                                                           ms_step * 1e-3))
@@ -704,7 +765,7 @@ def main():
             line["cpu_baseline"] = cpu_baseline(n, args.seed)
         summary = summary_fields(line)
         # scalars first, after the contract's keys; the large leg objects last
-        legs = {k: line.pop(k) for k in ("lhaf", "batched", "serving", "lowrank", "precision") if k in line}
+        legs = {k: line.pop(k) for k in ("lhaf", "batched", "serving", "lowrank", "sweep", "precision") if k in line}
         line.update(summary)
         line.update(legs)
         print(json.dumps(line), flush=True)
