@@ -126,10 +126,16 @@ inline bool kind_mixed(int kind) { return kind >= kKindC64; }
 //   tile : N x ld bulk elements; after La Budde its first 4 (h+1) series
 //          elements hold the power-series arrays (GS, AC, ES, AC2), so it is
 //          at least that large
-//   vec  : W, P, TV (and VA, VB for the loop hafnian), N bulk elements each
-//   dnb  : La Budde's output, h+1 bulk elements (ub: loop moments, h+1)
+//   vec  : W, P, TV (and VA for the loop hafnian), N bulk elements each; the
+//          loop hafnian's b = X v^T is gathered into P, which the Krylov
+//          start reads before its first pass writes P
+//   dnb  : La Budde's output, h+1 bulk elements (ub: loop moments, h+1);
+//          for the loop hafnian with N >= h+1 they take W and P, free by
+//          the time the moments and La Budde run
 //   dn   : h+1 series elements (u: loop moments), equal to dnb / ub in FP64
-//   pos  : h ints, the pair list of the subset
+//   pos  : h ints, the pair list of the subset (dead after the gather; the
+//          loop hafnian then keeps b's first entry, beta, in its first 16
+//          bytes)
 struct SubsetLayout {
   int vec, dnb, ub, dn, u, pos, total;
 };
@@ -139,9 +145,20 @@ inline __host__ __device__ SubsetLayout subset_layout(int N, int ld, int h, int 
   SubsetLayout L;
   const int tile = N * ld * sb, ser = 4 * (h + 1) * ss;
   L.vec = round16(tile > ser ? tile : ser);
-  L.dnb = L.vec + (loops ? 5 : 3) * N * sb;
-  L.ub = L.dnb + (h + 1) * sb;
-  int end = L.ub + (loops ? (h + 1) * sb : 0);
+  int end;
+  if (!loops) {  // W, P, TV; La Budde's output
+    L.dnb = L.vec + 3 * N * sb;
+    L.ub = L.dnb;
+    end = L.dnb + (h + 1) * sb;
+  } else if (N >= h + 1) {  // W, P, TV, VA; La Budde's output in W, the moments in P
+    L.dnb = L.vec;
+    L.ub = L.vec + N * sb;
+    end = L.vec + 4 * N * sb;
+  } else {  // W, P, TV, VA; La Budde's output; the moments
+    L.dnb = L.vec + 4 * N * sb;
+    L.ub = L.dnb + (h + 1) * sb;
+    end = L.ub + (h + 1) * sb;
+  }
   if (mixed) {
     L.dn = round16(end);
     L.u = L.dn + (h + 1) * ss;

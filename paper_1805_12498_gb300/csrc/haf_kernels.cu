@@ -585,8 +585,8 @@ __device__ __forceinline__ void finish_step(int N, int k1, const T* __restrict__
 // the loop moments cheap.
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__ W, T* __restrict__ P,
-                            T* __restrict__ TV, T* VA, T* VB, bool loops, int g,
+__device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__ W, T* P,
+                            T* __restrict__ TV, T* VA, const T* VB, T* beta, bool loops, int g,
                             int G) {
   using O = Ops<T>;
   using R = typename O::R;
@@ -600,12 +600,16 @@ __device__ void householder(T* __restrict__ tile, int ld, int N, T* __restrict__
     T w0, alpha;
     O::reflector(x0, s0, s0 + sig, c, w0, alpha);
     for (int i = 1 + g; i < N; i += G) W[i] = O::scale(VB[i], c);
-    if (g == 0) W[0] = w0;
+    if (g == 0) {
+      W[0] = w0;
+      *beta = alpha;  // b is now alpha e_0
+    }
+    // VB may share P's storage: every read of it is done before this
+    // barrier, and the dot pass below writes P
     __syncwarp();
     dot_pass<T>(tile, ld, N, 0, W, P, TV, g, G);
     __syncwarp();
     finish_step<T>(N, 0, W, P, VA, true, g, G);
-    for (int i = g; i < N; i += G) VB[i] = (i == 0) ? alpha : O::zero();
     __syncwarp();
     update_pass<T>(tile, ld, N, 0, W, TV, P, g, G);
     __syncwarp();
@@ -908,7 +912,8 @@ __device__ void process_chunk(const Job& job, const Chunk& ch, double* __restric
   // arrays of the subset (never written then), so that every pointer stays
   // inside the subset's region
   TB* VA = loops ? TV + N : W;
-  TB* VB = loops ? TV + 2 * N : W;
+  TB* VB = loops ? P : W;  // b = X v^T: read by the Krylov start before P is written
+  TB* beta = reinterpret_cast<TB*>(base + lay.pos);  // b's first entry after the Krylov start
   TB* Ub = loops ? reinterpret_cast<TB*>(base + lay.ub) : DNb;
   TS* U = loops ? reinterpret_cast<TS*>(base + lay.u) : DN;
   TS* GS = reinterpret_cast<TS*>(base);
@@ -956,8 +961,8 @@ __device__ void process_chunk(const Job& job, const Chunk& ch, double* __restric
       }
     }
     __syncwarp();
-    householder<TB>(tile, ld, N, W, P, TV, VA, VB, loops, g, G);
-    if (loops) loop_moments<TB>(tile, ld, N, h, VA, VB, W, TV, Ub, g, G);
+    householder<TB>(tile, ld, N, W, P, TV, VA, VB, beta, loops, g, G);
+    if (loops) loop_moments<TB>(tile, ld, N, h, VA, beta, W, TV, Ub, g, G);
     labudde<TB>(tile, ld, N, h, DNb, g, G);
     if constexpr (kMixed) {
       // widen the coefficients (and loop moments) for the FP64 series

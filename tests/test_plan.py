@@ -39,11 +39,15 @@ def _fits(N, h, sb, ss, mixed, warp_bytes, loops=False):
     """One subset fits a warp slice (mirror of the planner's rule, written
     from the layout the kernel documents: the N x ld tile, which also holds
     the four power-series arrays once La Budde is done; W, P, TV and, for
-    lhaf, VA, VB; La Budde's output (and the loop moments); in the FP32 mode
+    lhaf, VA (b is gathered into P); La Budde's output and, for lhaf, the
+    loop moments, which for N >= h + 1 reuse W and P; in the FP32 mode
     their FP64 copies; the pair list)."""
     for ld in (N + 1, N):
         b = _r16(max(N * ld * sb, 4 * (h + 1) * ss))
-        b += (5 if loops else 3) * N * sb + (2 if loops else 1) * (h + 1) * sb
+        if not loops:
+            b += 3 * N * sb + (h + 1) * sb
+        else:
+            b += 4 * N * sb + (0 if N >= h + 1 else 2 * (h + 1) * sb)
         if mixed:
             b = _r16(b) + (2 if loops else 1) * (h + 1) * ss
         b = _r16(_r16(b) + 4 * h)
@@ -61,10 +65,11 @@ def test_large_tiles_fall_back_to_fewer_warps():
     big = sum(comb(h, m) for m in range(1, h + 1) if not _fits(2 * m, h, 16, 16, False, 29056))
     assert big == sum(comb(h, m) for m in range(21, h + 1))
     assert s[6] == big and s[5] == 2 ** h - 1 - big
-    # the loop hafnian's extra vectors push |Z| = 20 out as well
+    # the loop hafnian's extra vector (VA) still fits |Z| = 20, because its
+    # moments and La Budde's output reuse W and P
     s = stats(48, _native.HAF_FLAG_LOOPS, 8)
     big = sum(comb(h, m) for m in range(1, h + 1) if not _fits(2 * m, h, 16, 16, False, 29056, True))
-    assert big == sum(comb(h, m) for m in range(20, h + 1))
+    assert big == sum(comb(h, m) for m in range(21, h + 1))
     assert s[6] == big
     # with 4 warps per CTA everything fits one launch
     s = stats(48, 0, 4)
