@@ -174,6 +174,7 @@ struct haf_server {
   std::map<uint64_t, std::unique_ptr<JobRec>> jobs;
   std::vector<int> free_slots;
   std::vector<unsigned int> slot_gen;
+  std::vector<JobRec*> pub_order;  // scheduler scratch: ready jobs in publication order
   uint64_t next_ticket = 1;
   cudaEvent_t kernel_done = nullptr;
   bool kernel_launched = false;
@@ -390,7 +391,8 @@ void scheduler(haf_server* s) {
           cudaEventRecord(s->claimed_ev, s->status) == cudaSuccess)
         s->claimed_pending = true;
     }
-    std::vector<JobRec*> order;
+    std::vector<JobRec*>& order = s->pub_order;  // reused: no allocation per pass
+    order.clear();
     for (auto& kv : s->jobs)
       if (kv.second->state == kReady && !kv.second->all_published()) order.push_back(kv.second.get());
     std::stable_sort(order.begin(), order.end(),
