@@ -140,6 +140,28 @@ struct SubsetLayout {
   int vec, dnb, ub, dn, u, pos, total;
 };
 inline __host__ __device__ int round16(int b) { return (b + 15) & ~15; }
+
+// Walk of lane g over the elements g, g + G, g + 2G, ... of a row-major
+// block with L columns: (i, j) = (e / L, e % L) for element e, stepped with
+// two divisions per walk instead of one per element (G / L and G % L are
+// fixed; one carry per step since j + G % L < 2 L).
+struct BlockWalk {
+  int i, j, di, dj, L;
+  __host__ __device__ __forceinline__ BlockWalk(int g, int G, int cols) : L(cols) {
+    i = g / L;
+    j = g - i * L;
+    di = G / L;
+    dj = G - di * L;
+  }
+  __host__ __device__ __forceinline__ void next() {
+    i += di;
+    j += dj;
+    if (j >= L) {
+      j -= L;
+      ++i;
+    }
+  }
+};
 inline __host__ __device__ SubsetLayout subset_layout(int N, int ld, int h, int sb, int ss, bool mixed,
                                                       bool loops) {
   SubsetLayout L;

@@ -535,14 +535,15 @@ __device__ __forceinline__ void update_pass(T* __restrict__ tile, int ld, int N,
                                             const T* __restrict__ TV, const T* __restrict__ Q, int g, int G) {
   using O = Ops<T>;
   const int L = N - k1;
-  for (int e = g; e < k1 * L; e += G) {
-    const int i = (int)((unsigned)e / (unsigned)L), j = k1 + e - i * L;
+  BlockWalk w1(g, G, L);  // element e = w1.i * L + w1.j of the rows above K
+  for (int e = g; e < k1 * L; e += G, w1.next()) {
+    const int i = w1.i, j = k1 + w1.j;
     T* a = tile + i * ld + j;
     *a = O::fnma_cb(Q[i], W[j], *a);
   }
-  for (int e = g; e < L * L; e += G) {
-    const int ii = (int)((unsigned)e / (unsigned)L);
-    const int i = k1 + ii, j = k1 + e - ii * L;
+  BlockWalk w2(g, G, L);  // element e = w2.i * L + w2.j of K x K
+  for (int e = g; e < L * L; e += G, w2.next()) {
+    const int i = k1 + w2.i, j = k1 + w2.j;
     T* a = tile + i * ld + j;
     const T v = O::fnma_cb(Q[i], W[j], *a);
     *a = O::fnma(W[i], TV[j], v);
@@ -947,8 +948,9 @@ __device__ void process_chunk(const Job& job, const Chunk& ch, double* __restric
     }
     __syncwarp();
     // gather B = (X A)^{(Z)}: B[r][c] = At[idx(r)][idx(c)], idx(r) = 2 pos[r/2] + (r&1)
-    for (int e = g; e < N * N; e += G) {
-      const int r = e / N, c = e - r * N;
+    BlockWalk wg(g, G, N);  // element e = r * N + c
+    for (int e = g; e < N * N; e += G, wg.next()) {
+      const int r = wg.i, c = wg.j;
       const int ir = 2 * pos[r >> 1] + (r & 1), ic = 2 * pos[c >> 1] + (c & 1);
       tile[r * ld + c] = valid ? OB::load(job.At, (size_t)ir * n + ic) : OB::zero();
     }
