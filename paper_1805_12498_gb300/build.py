@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhafnian_gb300.so")
 SOURCES = ["haf_kernels.cu", "haf_capi.cu", "haf_server.cu", "haf_lowrank.cu"]
-HEADERS = ["haf_internal.h", os.path.join("..", "..", "include", "hafnian_gb300.h")]
+HEADERS = ["haf_internal.h", "haf_nvtx.h", os.path.join("..", "..", "include", "hafnian_gb300.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -28,6 +28,7 @@
 
 #include "../../include/hafnian_gb300.h"
 #include "haf_internal.h"
+#include "haf_nvtx.h"
 
 using namespace hafgb;
 
@@ -424,6 +425,7 @@ int accuracy_gate(double rel, int prec, const char* where) {
 
 // Synchronous single matrix from host memory.
 int run_single(const double* A, int64_t n64, int loops, int is_real, int prec, double* out, haf_info* info) {
+  const NvtxRange nvtx_range("haf_single");
   const double t0 = now_s();
   if (n64 < 0 || n64 > kMaxN) return fail(HAF_EINVAL, "n out of range");
   if (prec == kPrecF32 && n64 > HAF_FP32_MAX_N) return fail(HAF_EINVAL, "FP32 mode: n above HAF_FP32_MAX_N");
@@ -508,6 +510,7 @@ int run_single(const double* A, int64_t n64, int loops, int is_real, int prec, d
 // the whole-matrix entry points (the value goes to part 0).
 int run_part(const double* A, int64_t n64, int loops, int is_real, int prec, int64_t part, int64_t nparts,
              double* rec, haf_info* info) {
+  const NvtxRange nvtx_range("haf_part");
   const double t0 = now_s();
   if (n64 < 0 || n64 > kMaxN) return fail(HAF_EINVAL, "n out of range");
   if (prec == kPrecF32 && n64 > HAF_FP32_MAX_N) return fail(HAF_EINVAL, "FP32 mode: n above HAF_FP32_MAX_N");
@@ -780,6 +783,7 @@ void stage_batch(const BatchPlan& bp, const double* const* As, const int64_t* ns
 
 int run_batched(const double* const* As, const int64_t* ns, int64_t count, int loops, int prec, double* outs,
                 haf_info* infos) {
+  const NvtxRange nvtx_range("haf_batched");
   const double t0 = now_s();
   if (count > 0 && !outs) return fail(HAF_EINVAL, "null pointer");
   std::vector<int> sizes;
@@ -952,6 +956,7 @@ size_t haf_workspace_bytes(int64_t n, uint32_t flags) {
 
 int haf_launch(const double* dA, int64_t n, uint32_t flags, double* d_out, void* d_work, size_t ws_bytes,
                void* stream) {
+  const NvtxRange nvtx_range("haf_launch");
   if (n < 2 || n > kMaxN || (n & 1)) return fail(HAF_EINVAL, "haf_launch: n must be even, 2..HAF_MAX_N");
   if (!dA || !d_out || !d_work) return fail(HAF_EINVAL, "haf_launch: null pointer");
   if (((uintptr_t)d_work & 255) != 0) return fail(HAF_EINVAL, "haf_launch: workspace not 256-byte aligned");
@@ -983,6 +988,7 @@ int haf_terms_c128(const double* A, int64_t n64, int loops, const uint64_t* mask
 }
 
 int haf_terms(const double* A, int64_t n64, uint32_t flags, const uint64_t* masks, int64_t count, double* terms) {
+  const NvtxRange nvtx_range("haf_terms");
   if (n64 < 2 || n64 > kMaxN || (n64 & 1)) return fail(HAF_EINVAL, "haf_terms: n must be even, 2..HAF_MAX_N");
   if (!A || (count > 0 && (!masks || !terms)) || count < 0) return fail(HAF_EINVAL, "haf_terms: bad arguments");
   if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_FP32)) return fail(HAF_EINVAL, "haf_terms: unknown flags");
@@ -1179,6 +1185,7 @@ bool same_cfg(const PlanCfg& a, const PlanCfg& b) {
 extern "C" {
 
 int haf_tune(int64_t n64, uint32_t flags, int32_t reps, haf_tune_result* out) {
+  const NvtxRange nvtx_range("haf_tune");
   if (n64 < 2 || n64 > kMaxN || (n64 & 1)) return fail(HAF_EINVAL, "haf_tune: n must be even, 2..HAF_MAX_N");
   if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_REAL | HAF_FLAG_FP32)) return fail(HAF_EINVAL, "haf_tune: unknown flags");
   if (reps < 1 || reps > 100 || !out) return fail(HAF_EINVAL, "haf_tune: reps must be 1..100, out non-null");
@@ -1255,6 +1262,7 @@ int haf_tune_set(int64_t n64, uint32_t flags, int32_t warps_per_block, int32_t c
 
 int haf_batched_tune(const double* const* As, const int64_t* ns, int64_t count, uint32_t flags, int32_t reps,
                      haf_tune_result* out) {
+  const NvtxRange nvtx_range("haf_batched_tune");
   if (flags & ~(HAF_FLAG_LOOPS | HAF_FLAG_FP32)) return fail(HAF_EINVAL, "haf_batched_tune: unknown flags");
   if (reps < 1 || reps > 100 || !out) return fail(HAF_EINVAL, "haf_batched_tune: reps must be 1..100, out non-null");
   const int loops = (flags & HAF_FLAG_LOOPS) ? 1 : 0, prec = (flags & HAF_FLAG_FP32) ? kPrecF32 : kPrecF64;

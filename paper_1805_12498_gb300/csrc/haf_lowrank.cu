@@ -48,6 +48,7 @@
 
 #include "../../include/hafnian_gb300.h"
 #include "haf_internal.h"
+#include "haf_nvtx.h"
 
 namespace hafgb {
 namespace {
@@ -668,6 +669,7 @@ extern "C" size_t haf_lowrank_workspace_bytes(int64_t n, int64_t r) {
 
 extern "C" int haf_lowrank_launch(const double* dG, int64_t n64, int64_t r64, double* d_out, void* d_work,
                                   size_t ws_bytes, void* stream) {
+  const NvtxRange nvtx_range("haf_lowrank_launch");
   if (!dG || !d_out || !d_work || n64 < 2 || n64 > HAF_LOWRANK_MAX_N || (n64 & 1) || r64 < 1 ||
       r64 > HAF_LOWRANK_MAX_R)
     return lfail(HAF_EINVAL, "haf_lowrank_launch: need device pointers, even 2 <= n <= HAF_LOWRANK_MAX_N, "
@@ -684,6 +686,7 @@ extern "C" int haf_lowrank_launch(const double* dG, int64_t n64, int64_t r64, do
 }
 
 extern "C" int haf_lowrank_c128(const double* G, int64_t n64, int64_t r64, double* out, haf_info* info) {
+  const NvtxRange nvtx_range("haf_lowrank");
   if (!out || n64 < 0 || n64 > HAF_LOWRANK_MAX_N || r64 < 1 || r64 > HAF_LOWRANK_MAX_R || (n64 > 0 && !G))
     return lfail(HAF_EINVAL, "haf_lowrank_c128: need 0 <= n <= HAF_LOWRANK_MAX_N, 1 <= r <= HAF_LOWRANK_MAX_R");
   const int n = (int)n64, r = (int)r64;

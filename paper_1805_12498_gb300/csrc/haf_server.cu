@@ -39,6 +39,7 @@
 
 #include "../../include/hafnian_gb300.h"
 #include "haf_internal.h"
+#include "haf_nvtx.h"
 
 using namespace hafgb;
 
@@ -569,6 +570,7 @@ int haf_server_create(const haf_server_cfg* cfg, haf_server** out) {
 }
 
 int haf_server_submit(haf_server* s, int kind, const double* A, int64_t n, uint64_t* ticket) {
+  const NvtxRange nvtx_range("haf_server_submit");
   if (!s || !ticket || (kind != 0 && kind != 1)) return sfail(HAF_EINVAL, "haf_server_submit: bad arguments");
   if (n < 0 || n > kMaxN || (n > 0 && !A)) return sfail(HAF_EINVAL, "haf_server_submit: n out of range or null A");
   std::unique_ptr<JobRec> j(new JobRec());
@@ -608,6 +610,7 @@ int haf_server_submit(haf_server* s, int kind, const double* A, int64_t n, uint6
 }
 
 int haf_server_poll(haf_server* s, uint64_t ticket, double* out, haf_info* info, int64_t timeout_us) {
+  const NvtxRange nvtx_range("haf_server_poll");
   if (!s || !out) return sfail(HAF_EINVAL, "haf_server_poll: bad arguments");
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->jobs.find(ticket);
