@@ -377,13 +377,15 @@ def hbm_peak_gbs() -> float:
         return 6800.0
 
 
-def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
+def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7, rate: float = 0.0):
     """Serving: haf/lhaf requests (50/50) on GBS
     submatrices, n even in [8, n_max] with P(n) proportional to 2^(-n/8),
     through the continuous-batching server.  The capacity is measured first
     with all requests submitted at once; the open-loop run then offers
     Poisson arrivals at `load` x capacity and reports throughput and the
-    p50/p99 of the submit-to-result latency the server records."""
+    p50/p99 of the submit-to-result latency the server records.  With
+    rate > 0 (requests/s) the open-loop run alone is made at that rate:
+    no capacity run and no one-launch comparison, for long streams."""
     import threading as th
 
     import paper_1805_12498_gb300 as hg
@@ -400,12 +402,14 @@ def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
     with hg.Server() as srv:
         for M, loops in reqs[:16]:  # warm the resident kernel and the plans
             srv.poll(srv.submit(M, loops), timeout_s=3600)
-        t = time.perf_counter()
-        tickets = [srv.submit(M, loops) for M, loops in reqs]
-        for tk in tickets:
-            srv.poll(tk, timeout_s=3600)
-        capacity = requests / (time.perf_counter() - t)
-        rate = load * capacity
+        capacity = None
+        if rate <= 0:
+            t = time.perf_counter()
+            tickets = [srv.submit(M, loops) for M, loops in reqs]
+            for tk in tickets:
+                srv.poll(tk, timeout_s=3600)
+            capacity = requests / (time.perf_counter() - t)
+            rate = load * capacity
         gaps = g.exponential(1.0 / rate, size=requests)
         submitted = []
         lock = th.Lock()
@@ -437,6 +441,15 @@ def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
             k += 1
         thr.join()
         wall = time.perf_counter() - t0
+    lat = np.array(lat) * 1e3
+    if capacity is None:
+        return {"workload": f"{requests} requests, haf/lhaf 50/50, GBS submatrices of a 32-mode kernel (r=0.88), "
+                            f"n even in [8,{n_max}], P(n) ~ 2^(-n/8), Poisson arrivals at {rate:g} req/s",
+                "offered_req_per_s": rate, "throughput_req_per_s": requests / wall,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_ms": float(lat.max()), "jobs_by_n": {int(k): int(v) for k, v in
+                                                         zip(*np.unique([M.shape[0] for M, _ in reqs],
+                                                                        return_counts=True))}}
     # the same requests, one synchronous single-matrix call each (the plain
     # one-launch-per-hafnian form) on the same GPU: its capacity, and its
     # latency under the same Poisson arrivals with one FIFO worker
@@ -465,7 +478,6 @@ def serving_leg(requests: int, n_max: int, seed: int, load: float = 0.7):
         fifo.append(time.perf_counter() - t_arr)
     thr.join()
     fifo = np.array(fifo) * 1e3
-    lat = np.array(lat) * 1e3
     return {"workload": f"{requests} requests, haf/lhaf 50/50, GBS submatrices of a 32-mode kernel (r=0.88), "
                         f"n even in [8,{n_max}], P(n) ~ 2^(-n/8), Poisson arrivals at {load:g} x capacity",
             "capacity_req_per_s": capacity, "offered_req_per_s": rate, "throughput_req_per_s": requests / wall,
@@ -521,11 +533,13 @@ def summary_fields(line: dict) -> dict:
         out["batched_speedup_vs_one_launch_per_haf"] = line["batched"]["speedup_vs_one_launch_per_haf"]
     if "serving" in line:
         sv = line["serving"]
-        out["serving_capacity_vs_one_launch"] = sv["capacity_vs_one_launch"]
+        if "capacity_vs_one_launch" in sv:
+            out["serving_capacity_vs_one_launch"] = sv["capacity_vs_one_launch"]
         out["serving_p50_ms"] = sv["p50_ms"]
         out["serving_p99_ms"] = sv["p99_ms"]
-        out["one_launch_fifo_p50_ms"] = sv["one_launch_fifo_p50_ms"]
-        out["one_launch_fifo_p99_ms"] = sv["one_launch_fifo_p99_ms"]
+        if "one_launch_fifo_p50_ms" in sv:
+            out["one_launch_fifo_p50_ms"] = sv["one_launch_fifo_p50_ms"]
+            out["one_launch_fifo_p99_ms"] = sv["one_launch_fifo_p99_ms"]
     if "sweep" in line:
         for row in line["sweep"]["rows"]:
             if row["n"] == max(r["n"] for r in line["sweep"]["rows"]) and row["dtype"] == "c128":
@@ -631,6 +645,8 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32-vs-FP64 precision leg")
     ap.add_argument("--no-lhaf", action="store_true", help="skip the loop-hafnian leg")
     ap.add_argument("--no-lowrank", action="store_true", help="skip the low-rank (App. C) leg")
+    ap.add_argument("--serve-rate", type=float, default=0.0,
+                    help="serving leg: offer this many requests/s and skip the capacity and one-launch runs")
     ap.add_argument("--no-sweep", action="store_true", help="skip the n = 24..52 size sweep")
     ap.add_argument("--sweep-sizes", default="24,28,32,36,40,44,48,52",
                     help="sizes of the sweep leg (n = 56 adds about six minutes)")
@@ -753,7 +769,7 @@ def main():
         if args.gbs_batch > 0 and world == 1:
             line["batched"] = batched_leg(args.gbs_batch, args.seed)
         if args.serve_requests > 0 and world == 1:
-            line["serving"] = serving_leg(args.serve_requests, args.serve_nmax, args.seed)
+            line["serving"] = serving_leg(args.serve_requests, args.serve_nmax, args.seed, rate=args.serve_rate)
         if not args.no_lowrank and world == 1:
             line["lowrank"] = lowrank_leg(args.seed)
         if not args.no_sweep and world == 1:
