@@ -87,3 +87,17 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "16",
                         "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=120, env=env)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_summary_fields_with_a_fixed_rate_serving_leg():
+    """--serve-rate runs the open-loop stream alone: the summary keeps its
+    latencies and leaves out the capacity and one-launch fields."""
+    line = {"ms_per_step": 1000.0,
+            "serving": {"offered_req_per_s": 3.0, "throughput_req_per_s": 2.9, "p50_ms": 12.0, "p99_ms": 900.0,
+                        "max_ms": 5000.0}}
+    out = bench.summary_fields(line)
+    assert out == {"serving_p50_ms": 12.0, "serving_p99_ms": 900.0}
+    line["serving"].update({"capacity_vs_one_launch": 1.01, "one_launch_fifo_p50_ms": 100.0,
+                            "one_launch_fifo_p99_ms": 2000.0})
+    out = bench.summary_fields(line)
+    assert out["serving_capacity_vs_one_launch"] == 1.01 and out["one_launch_fifo_p99_ms"] == 2000.0
