@@ -101,3 +101,49 @@ def test_summary_fields_with_a_fixed_rate_serving_leg():
                             "one_launch_fifo_p99_ms": 2000.0})
     out = bench.summary_fields(line)
     assert out["serving_capacity_vs_one_launch"] == 1.01 and out["one_launch_fifo_p99_ms"] == 2000.0
+
+
+class _FakeResult:
+    def __init__(self, seconds):
+        self.seconds = seconds
+        self.value = 0j
+
+
+class _FakeServer:
+    """Stands in for hg.Server on the CPU: every request finishes at once
+    with a latency of 1 ms."""
+
+    def __init__(self, *a, **k):
+        self.n = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+    def submit(self, M, loops=False):
+        self.n += 1
+        return self.n
+
+    def poll(self, ticket, timeout_s=None):
+        return _FakeResult(0.001)
+
+
+@pytest.mark.parametrize("rate", [0.0, 500.0])
+def test_serving_leg_logic_on_a_fake_server(monkeypatch, rate):
+    """Both forms of the serving leg (with the capacity and one-launch runs,
+    and the fixed-rate stream alone) run through and report their fields."""
+    import paper_1805_12498_gb300 as hg
+    monkeypatch.setattr(hg, "Server", _FakeServer)
+    monkeypatch.setattr(hg, "haf_info", lambda M, loops=False: _FakeResult(0.0))
+    out = bench.serving_leg(24, 12, seed=3, rate=rate)
+    assert out["p50_ms"] == pytest.approx(1.0) and out["p99_ms"] == pytest.approx(1.0)
+    assert out["throughput_req_per_s"] > 0
+    if rate > 0:
+        assert out["offered_req_per_s"] == rate and "capacity_req_per_s" not in out
+        assert sum(out["jobs_by_n"].values()) == 24
+    else:
+        assert out["capacity_req_per_s"] > 0 and out["capacity_vs_one_launch"] > 0
+        assert out["one_launch_fifo_p99_ms"] >= 0
+    json.dumps(out)  # the record is plain JSON
